@@ -1,0 +1,388 @@
+#!/usr/bin/env python3
+"""Benchmark of the cascaded-biquad hot path on GB300.
+
+One step = one full call of the C ABI's sos_filter (plan kernel + fused
+filtering kernel) on the 16th-order (K = 8) Butterworth band-pass workload,
+2^24 FP32 samples i.i.d. N(0, 1), one channel, zero initial state, inputs
+resident in HBM.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Multi-GPU (torchrun, one process per GPU): the single long signal does not
+shard without a state exchange, so each rank filters its own replica of the
+workload (weak scaling, no data-path collective); a barrier and a max over
+ranks bracket the timing.
+
+The L2 cache (126.5 MiB on GB300) is flushed between timed steps by writing a
+256 MiB buffer, outside the timed events.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SM_COUNT_NOMINAL = 152
+FP32_LANES_PER_SM = 128
+
+
+def fma_per_sample(K: int) -> int:
+    # the method's own count: 6 block FMAs per sample per section
+    # (paper Table overall_complexity, dominant term 6/L per lane-sample) plus
+    # one multiply for the split-off gain (Sec. II, Eq. simple_second_order)
+    return 6 * K + 1
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the GPU is under load."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "utilization.gpu")
+
+    def __init__(self, gpu_index: int, out_path: str | None):
+        self.gpu = gpu_index
+        self.out_path = out_path
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.out_path:
+            with open(self.out_path, "w") as f:
+                f.write(self.FIELDS + "\n")
+                for _, l in self.lines:
+                    f.write(l + "\n")
+        rows = []
+        for _, l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 10:
+                continue
+            try:
+                rows.append({"sm": float(parts[1]), "max": float(parts[2]),
+                             "hw": parts[5], "hwt": parts[6], "swt": parts[7], "pcap": parts[8],
+                             "util": float(parts[9])})
+            except ValueError:
+                continue
+        load = [r for r in rows if r["util"] > 0] or rows
+        if not load:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        reasons = set()
+        for r in load:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in load),
+                "sm_max_mhz": max(r["max"] for r in load), "reasons": sorted(reasons),
+                "samples": len(load)}
+
+
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def oracle_baseline(wl, target_seconds: float = 10.0):
+    """Times the FP64 oracle (as it stands) on the host cores: whole-signal
+    passes of the workload, repeated until ~target_seconds of CPU work."""
+    import numpy as np
+    import oracle
+    x = wl.x.detach().cpu().double().numpy()
+    sos = wl.sos.cpu().numpy()
+    K = wl.K.cpu().numpy()
+    lengths = wl.lengths.numpy()
+    reps = 0
+    t0 = time.perf_counter()
+    while True:
+        oracle.sosfilt(x, sos, K=K, lengths=lengths)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= target_seconds or reps >= 50:
+            break
+    samples = x.size * reps
+    threads = min(oracle.num_threads(), wl.n_channels)
+    return {"value": samples / el / 1e9, "unit": "Gsamples/s", "cores": int(threads),
+            "kind": "oracle",
+            "sample": f"{reps} full passes of the {x.size}-sample workload ({el:.1f} s); "
+                      f"FP64 sample-by-sample cascade, one thread per channel",
+            "seconds": el}
+
+
+def run_reference(args):
+    rank, world, local = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    from synth import workloads
+    wl = workloads.plain_bandpass16(n=1 << 24, device="cpu")
+    import oracle
+    x = wl.x.double().numpy()
+    sos = wl.sos.numpy()
+    # each step is a bounded sample of the workload: the first 2^21 samples
+    # (causal: these outputs equal the full run's first 2^21)
+    n = 1 << 21
+    xs = x[:n]
+    for _ in range(max(args.warmup, 0)):
+        oracle.sosfilt(xs, sos)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sosfilt(xs, sos)
+    el = time.perf_counter() - t0
+    value = n * args.steps / el / 1e9
+    line = {
+        "impl": "reference", "metric": "Gsamples/s K=8 FP32 (batched/plain) and % roofline at "
+        "rel-L2<=1e-5 vs FP64", "value": value, "unit": "Gsamples/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "samples_per_step": n, "channels": 1, "sections": 8},
+        "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} samples of the 2^24-sample signal per step"},
+        "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--tuning", default="", help="N,W (e.g. 32,8)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--clock-seconds", type=float, default=2.0)
+    ap.add_argument("--clocks-out", default="")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2607_14054_gb300 as P
+    from synth import workloads
+
+    wl = workloads.plain_bandpass16(n=1 << 24, device=dev)
+    Kmax = wl.kmax
+    tuning = tuple(int(v) for v in args.tuning.split(",")) + (0, 0) if args.tuning else None
+    tuning = tuning[:4] if tuning else None
+    plan = P.SosFilter(wl.lengths, Kmax, tuning=tuning, device=dev)
+    x = wl.x
+    sos = wl.sos
+    K = wl.K
+    y = torch.empty_like(x)
+    zf = torch.empty(wl.n_channels, Kmax, 2, dtype=torch.float32, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step():
+        plan.prepare(sos, K)
+        plan.apply(x, y, None, zf)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    st = plan.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+
+    stream = torch.cuda.current_stream(dev)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        plan.prepare(sos, K)
+        ev[i][1].record(stream)
+        plan.apply(x, y, None, zf)
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall0
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    apply_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    prep_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    ms_per_step = sum(step_ms) / len(step_ms)
+    ms_apply = sum(apply_ms) / len(apply_ms)
+    ms_per_step = reduce_max(ms_per_step, world)
+    ms_apply = reduce_max(ms_apply, world)
+    samples = wl.total
+    value = samples * world / (ms_per_step * 1e-3) / 1e9
+
+    # sustained loop with clock sampling (same steps, untimed)
+    sampler = ClockSampler(local, args.clocks_out or None)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = time.perf_counter()
+    n_sus = 0
+    while time.perf_counter() - t0 < args.clock_seconds:
+        for _ in range(50):
+            flush.zero_()
+            step()
+            n_sus += 1
+        torch.cuda.synchronize()
+    clocks = sampler.stop()
+
+    # end to end through the public API: pinned host input -> device ->
+    # filter -> host output, every step
+    xh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x)
+    yh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
+    xd = torch.empty_like(x)
+    e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        step_e2e_y = P.sosfilt(xd, sos)
+        yh.copy_(step_e2e_y[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        xd.copy_(xh, non_blocking=True)
+        yd, zfd = P.sosfilt(xd, sos)
+        yh.copy_(yd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    e2e_ms = reduce_max(e2e_ms, world)
+    e2e_value = samples * world / (e2e_ms * 1e-3) / 1e9
+
+    # quick parity sanity on a prefix (causal: the first n outputs of the full
+    # run equal the oracle on the first n inputs)
+    parity = None
+    if rank == 0:
+        try:
+            import numpy as np
+            import oracle
+            n = 1 << 20
+            yref, _ = oracle.sosfilt(x[:n].double().cpu().numpy(), sos.cpu().numpy())
+            yg = y[:n].double().cpu().numpy()
+            parity = float(np.linalg.norm(yg - yref) / np.linalg.norm(yref))
+        except Exception as exc:  # noqa: BLE001
+            parity = f"unavailable: {exc}"
+
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    fmas = fma_per_sample(8)
+    achieved = 2.0 * fmas * samples / (ms_apply * 1e-3) / 1e12
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
+    roof_samples = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / fmas) / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(workloads.plain_bandpass16(n=1 << 24, device="cpu"))
+
+    line = {
+        "metric": "Gsamples/s K=8 FP32 (batched/plain) and % roofline at rel-L2<=1e-5 vs FP64",
+        "value": value,
+        "unit": "Gsamples/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_per_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "samples": samples, "channels": 1, "sections": 8,
+                   "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
+                   "tuning": list(plan.tuning), "step": "sos_prepare + sos_apply",
+                   "ms_prepare": sum(prep_ms) / len(prep_ms), "ms_apply": ms_apply,
+                   "roofline_gsamples_per_s": roof_samples,
+                   "frac_of_sample_roofline": value / world / roof_samples,
+                   "wall_s_timed": t_wall},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                     "kernel": "sos_forward_kernel", "flops_per_sample": 2 * fmas,
+                     "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
+                                    f"{sm_max:.0f} MHz ({src} max clock)"},
+        "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
+                "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
+                "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "parity_rel_l2_prefix": parity,
+        "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,153 @@
+/*
+ * sosfilt.h - C ABI of the GB300 (sm_103a) cascaded-biquad filter library.
+ *
+ * The library filters FP32 signals through a cascade of K second-order
+ * sections (biquads), paper Sec. II, Eq. general_cascaded_equation and
+ * Eq. complex_second_order:
+ *
+ *   y_k[n] = b0 x_k[n] + b1 x_k[n-1] + b2 x_k[n-2] - a1 y_k[n-1] - a2 y_k[n-2],
+ *   x_1 = x,  x_{k+1} = y_k,  y = y_K,
+ *
+ * every row first divided by its a0.  The result is the exact solution of the
+ * banded block-Toeplitz system of Sec. III, Eq. recursive_equation_block_form
+ * (up to FP32 rounding); it is computed with the stride-N multi-block
+ * formulation of Sec. V (lane l of a 32-lane warp owns the contiguous samples
+ * [lN, lN+N) of a group, i.e. register m of all lanes is the strided block
+ * x_m = [x[m], x[m+N], ...]), the PH factorisation of Sec. VI-B for the
+ * recursive stage, and one permutation / de-permutation pair per cascade
+ * (Sec. VII-B).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Pointers named "device" must point to device memory of the current CUDA
+ *   device.  The caller owns every buffer; the library never allocates device
+ *   memory and never frees anything.
+ * - Streams are passed as `void *` holding a cudaStream_t (NULL = the legacy
+ *   default stream).  All device work is enqueued on that stream and the call
+ *   returns without synchronising; nothing inside calls cudaMalloc or
+ *   synchronises the host, so calls may be captured into a CUDA graph.
+ * - Channels are packed: channel c occupies samples [off_c, off_c + len_c) of
+ *   x and y, off_c being the exclusive prefix sum of the lengths.  Any offset
+ *   alignment is accepted (16-byte-aligned channels take a faster load path).
+ * - sos rows are FP64 (b0, b1, b2, a0, a1, a2), shape [n_channels][kmax][6];
+ *   rows k >= K[c] are not read.  a0 must be nonzero.
+ * - State (zi, zf) is FP32 [n_channels][kmax][2] in the transposed direct
+ *   form II convention of scipy.signal.sosfilt: for section k,
+ *     z1 = b1 x[-1] + b2 x[-2] - a1 y[-1] - a2 y[-2],  z2 = b2 x[-1] - a2 y[-1],
+ *   which are exactly the two scalar corrections the paper adds to the first
+ *   element of the first two blocks (Sec. V-A, Eq. feedforward_block_uniform).
+ *   zf rows k >= K[c] are written as zero; a zero-length channel returns zi.
+ * - Errors in arguments are detected on the host and returned before any
+ *   work is enqueued.  Errors found on the device (nonzero a0 violated,
+ *   non-finite coefficients, an unstable section when the stability check is
+ *   on, a look-back wait that ran out) are written to a status word inside
+ *   the workspace; read it with sos_device_status().
+ */
+#ifndef SOSFILT_H
+#define SOSFILT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sos_status {
+    SOS_OK = 0,
+    SOS_ERR_ARG = -1,         /* bad argument (null pointer, size, kmax > 8, ...) */
+    SOS_ERR_UNSTABLE = -2,    /* a section has a pole on/outside the unit circle (check on) */
+    SOS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+    SOS_ERR_TIMEOUT = -4,     /* a cross-tile look-back wait exceeded its bound */
+    SOS_ERR_WORKSPACE = -5,   /* workspace too small or not initialised */
+    SOS_ERR_UNSUPPORTED = -6, /* tuning values outside the compiled set */
+    SOS_ERR_COEF = -7         /* a0 == 0 or a non-finite coefficient */
+} sos_status;
+
+/* Tuning knobs.  Pass NULL for the library defaults.
+ *   n_blocks: N, samples per lane per group (the paper's number of blocks):
+ *             16, 32 or 64 (0 = default 32).
+ *   warps:    W, warps per tile (one tile = W*32*N samples): 4, 8 or 16
+ *             (0 = default 8).
+ *   algo:     recursive-stage solver: 0 = default, 1 = PH (Sec. VI-B).
+ *   flags:    bit 0 (SOS_FLAG_CHECK_STABLE): reject sections whose poles are
+ *             not strictly inside the unit circle. */
+typedef struct sos_tuning {
+    int32_t n_blocks;
+    int32_t warps;
+    int32_t algo;
+    int32_t flags;
+} sos_tuning;
+
+#define SOS_FLAG_CHECK_STABLE 1
+#define SOS_MAX_SECTIONS 8
+
+/* Bytes of device workspace needed for a call with these sizes.
+ * lengths_host: host array [n_channels] of channel lengths (>= 0).
+ * Returns 0 if the arguments are invalid. */
+size_t sos_workspace_size(int32_t n_channels, int32_t kmax, const int64_t *lengths_host,
+                          const sos_tuning *tuning);
+
+/* Zero-initialise a workspace once, before its first use (stream-ordered
+ * memset).  A workspace may be reused by any number of later calls with sizes
+ * that fit, but calls sharing a workspace must not overlap on the GPU. */
+sos_status sos_workspace_init(void *workspace, size_t ws_bytes, void *stream);
+
+/* Forward cascade filter (the hot path).
+ *   x        device FP32 [sum len]            input signals, packed
+ *   sos      device FP64 [n_channels][kmax][6]
+ *   K        device int32 [n_channels]        sections per channel, 0..kmax
+ *   n_channels >= 1, 1 <= kmax <= 8
+ *   lengths       device int64 [n_channels]   channel lengths
+ *   lengths_host  host   int64 [n_channels]   the same values (used for sizing)
+ *   zi       device FP32 [n_channels][kmax][2] or NULL (zero initial state)
+ *   y        device FP32 [sum len]            output (must not overlap x)
+ *   zf       device FP32 [n_channels][kmax][2] or NULL
+ *   workspace / ws_bytes  device buffer of at least sos_workspace_size() bytes,
+ *                         initialised once by sos_workspace_init()
+ *   tuning   host pointer or NULL
+ *   stream   cudaStream_t as void*
+ * Returns SOS_OK once the work is enqueued. */
+sos_status sos_filter(const float *x, const double *sos, const int32_t *K, int32_t n_channels,
+                      int32_t kmax, const int64_t *lengths, const int64_t *lengths_host,
+                      const float *zi, float *y, float *zf, void *workspace, size_t ws_bytes,
+                      const sos_tuning *tuning, void *stream);
+
+/* The two halves of sos_filter, for callers that filter many signals with
+ * the same coefficients, section counts and lengths (or that time the
+ * filtering kernel alone).
+ *
+ * sos_prepare enqueues the plan kernel: the per-channel offsets and tile
+ * prefix, and the coefficient tables (normalisation by a0, the split-off
+ * gain of Sec. II, Eq. simple_second_order, and the transition-matrix powers,
+ * "pre-computed before filtering" as in Sec. VI-B, formed in FP64).  It also
+ * clears the workspace's device status word.
+ *
+ * sos_apply enqueues only the filtering kernel, reusing those tables; it may
+ * be called any number of times after one sos_prepare on the same workspace
+ * with the same K, lengths and tuning (x, y, zi and zf may change between
+ * calls).  Arguments mean what they mean in sos_filter.
+ *
+ * sos_filter == sos_prepare followed by sos_apply. */
+sos_status sos_prepare(const double *sos, const int32_t *K, int32_t n_channels, int32_t kmax,
+                       const int64_t *lengths, const int64_t *lengths_host, void *workspace,
+                       size_t ws_bytes, const sos_tuning *tuning, void *stream);
+sos_status sos_apply(const float *x, int32_t n_channels, int32_t kmax,
+                     const int64_t *lengths_host, const float *zi, float *y, float *zf,
+                     void *workspace, size_t ws_bytes, const sos_tuning *tuning, void *stream);
+
+/* Waits for `stream`, then returns (and clears) the device-side status word
+ * of the most recent call that used this workspace. */
+sos_status sos_device_status(void *workspace, void *stream);
+
+/* Human-readable name of a status code (static string). */
+const char *sos_status_str(sos_status status);
+
+/* Library version, for the bindings' sanity check. */
+int32_t sos_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOSFILT_H */

@@ -1,0 +1,164 @@
+"""Cascaded biquad (second-order-section) filtering on GB300 (sm_103a).
+
+The compute runs in the hand-written CUDA kernels of ``libsosfilt.so`` behind
+the C ABI of ``include/sosfilt.h``; this package only marshals PyTorch
+tensors (device memory and the current stream) into those calls.  There is
+no CPU fallback: without the compiled library and a CUDA device every entry
+point raises.
+
+    y, zf = sosfilt(x, sos)                        # one channel
+    y, zf = sosfilt(x, sos, K=K, lengths=lengths, zi=zi)   # packed batch
+
+``SosFilter`` keeps the workspace and the device copy of the lengths for
+repeated calls with the same shapes (and is what CUDA-graph capture uses).
+"""
+from __future__ import annotations
+
+from typing import Optional, Sequence
+
+import torch
+
+from . import _abi
+from ._abi import SosError, sos_tuning  # noqa: F401
+
+__all__ = ["SosFilter", "sosfilt", "SosError", "sos_tuning", "build"]
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib
+    return buildlib.build(force=force)
+
+
+def _check_device(t: torch.Tensor, name: str):
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (this library has no CPU path)")
+
+
+class SosFilter:
+    """A reusable plan: channel lengths, section count and tuning fixed;
+    signals, coefficients and states passed per call."""
+
+    def __init__(self, lengths: Sequence[int] | torch.Tensor, kmax: int,
+                 tuning: Optional[Sequence[int]] = None, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("sosfilt needs a CUDA device")
+        _abi.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        lh = torch.as_tensor(lengths, dtype=torch.int64).reshape(-1).cpu().contiguous()
+        if lh.numel() < 1:
+            raise ValueError("at least one channel")
+        if int(lh.min()) < 0:
+            raise ValueError("negative length")
+        self.lengths_host = lh
+        self.lengths = lh.to(self.device)
+        self.n_channels = int(lh.numel())
+        self.kmax = int(kmax)
+        self.total = int(lh.sum())
+        self.tuning = tuple(tuning) if tuning is not None else (0, 0, 0, 0)
+        nbytes = _abi.sos_workspace_size(self.n_channels, self.kmax, lh.data_ptr(), self.tuning)
+        if nbytes == 0:
+            raise ValueError("unsupported sizes or tuning %r" % (self.tuning,))
+        self.ws_bytes = nbytes
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = _abi.sos_workspace_init(self.workspace.data_ptr(), nbytes, stream)
+        if st != 0:
+            raise SosError(st, "sos_workspace_init")
+
+    def __call__(self, x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                 zi: Optional[torch.Tensor] = None, y: Optional[torch.Tensor] = None,
+                 zf: Optional[torch.Tensor] = None, want_zf: bool = True):
+        C, kmax = self.n_channels, self.kmax
+        _check_device(x, "x")
+        if x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != self.total:
+            raise ValueError("x must be contiguous float32 with sum(lengths) elements")
+        sos = sos.reshape(C, kmax, 6)
+        if sos.dtype != torch.float64 or not sos.is_contiguous() or sos.device != x.device:
+            raise ValueError("sos must be contiguous float64 [C, kmax, 6] on x's device")
+        if K is None:
+            K = torch.full((C,), kmax, dtype=torch.int32, device=x.device)
+        if K.dtype != torch.int32 or not K.is_contiguous() or K.numel() != C:
+            raise ValueError("K must be contiguous int32 [C]")
+        if zi is not None:
+            zi = zi.reshape(C, kmax, 2)
+            if zi.dtype != torch.float32 or not zi.is_contiguous():
+                raise ValueError("zi must be contiguous float32 [C, kmax, 2]")
+        if y is None:
+            y = torch.empty_like(x)
+        if zf is None and want_zf:
+            zf = torch.empty((C, kmax, 2), dtype=torch.float32, device=x.device)
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_filter(x.data_ptr(), sos.data_ptr(), K.data_ptr(), C, kmax,
+                             self.lengths.data_ptr(), self.lengths_host.data_ptr(),
+                             zi.data_ptr() if zi is not None else 0, y.data_ptr(),
+                             zf.data_ptr() if zf is not None else 0, self.workspace.data_ptr(),
+                             self.ws_bytes, self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_filter")
+        return y, zf
+
+    def prepare(self, sos: torch.Tensor, K: Optional[torch.Tensor] = None):
+        """Enqueue only the plan kernel (coefficient tables) for these sos/K."""
+        C, kmax = self.n_channels, self.kmax
+        sos = sos.reshape(C, kmax, 6)
+        if K is None:
+            K = torch.full((C,), kmax, dtype=torch.int32, device=sos.device)
+        self._keep = (sos, K)
+        stream = torch.cuda.current_stream(sos.device).cuda_stream
+        st = _abi.sos_prepare(sos.data_ptr(), K.data_ptr(), C, kmax, self.lengths.data_ptr(),
+                              self.lengths_host.data_ptr(), self.workspace.data_ptr(),
+                              self.ws_bytes, self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_prepare")
+
+    def apply(self, x: torch.Tensor, y: torch.Tensor, zi: Optional[torch.Tensor] = None,
+              zf: Optional[torch.Tensor] = None):
+        """Enqueue only the filtering kernel, using the tables of the last
+        prepare() on this plan."""
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_apply(x.data_ptr(), self.n_channels, self.kmax, self.lengths_host.data_ptr(),
+                            zi.data_ptr() if zi is not None else 0, y.data_ptr(),
+                            zf.data_ptr() if zf is not None else 0, self.workspace.data_ptr(),
+                            self.ws_bytes, self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_apply")
+        return y, zf
+
+    def device_status(self) -> int:
+        """Synchronises the current stream and returns the device-side status
+        of the latest call (0 = OK)."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        return _abi.sos_device_status(self.workspace.data_ptr(), stream)
+
+
+_plans = {}
+
+
+def sosfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+            lengths=None, zi: Optional[torch.Tensor] = None, tuning=None, check: bool = False):
+    """Filter x (float32, CUDA, packed channels) through the cascade ``sos``
+    (float64 [C, kmax, 6] or [kmax, 6]).  Returns (y, zf)."""
+    _check_device(x, "x")
+    if sos.dim() == 2:
+        sos = sos.unsqueeze(0)
+    C, kmax = int(sos.shape[0]), int(sos.shape[1])
+    if lengths is None:
+        if C != 1:
+            raise ValueError("lengths are required for more than one channel")
+        lengths = [x.numel()]
+    lh = tuple(int(v) for v in torch.as_tensor(lengths).reshape(-1).tolist())
+    key = (x.device, lh, kmax, tuple(tuning) if tuning is not None else None)
+    plan = _plans.get(key)
+    if plan is None:
+        plan = SosFilter(lh, kmax, tuning=tuning, device=x.device)
+        if len(_plans) > 16:
+            _plans.clear()
+        _plans[key] = plan
+    y, zf = plan(x.contiguous(), sos.contiguous(), K, zi)
+    if check:
+        st = plan.device_status()
+        if st != 0:
+            raise SosError(st, "sos_filter (device)")
+    return y, zf

@@ -1,0 +1,130 @@
+"""ctypes binding of the C ABI in include/sosfilt.h (argument marshalling only).
+
+Every function keeps the C name and argument order; pointers are passed as
+integers (``tensor.data_ptr()``), streams as the raw cudaStream_t handle.
+Loading fails loudly when the compiled library is missing: there is no
+fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import buildlib as _build
+
+_lock = threading.Lock()
+_lib = None
+
+SOS_OK = 0
+SOS_FLAG_CHECK_STABLE = 1
+SOS_MAX_SECTIONS = 8
+
+STATUS_NAMES = {
+    0: "SOS_OK", -1: "SOS_ERR_ARG", -2: "SOS_ERR_UNSTABLE", -3: "SOS_ERR_CUDA",
+    -4: "SOS_ERR_TIMEOUT", -5: "SOS_ERR_WORKSPACE", -6: "SOS_ERR_UNSUPPORTED", -7: "SOS_ERR_COEF",
+}
+
+
+class SosError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}")
+        self.status = status
+
+
+class sos_tuning(ctypes.Structure):
+    _fields_ = [("n_blocks", ctypes.c_int32), ("warps", ctypes.c_int32),
+                ("algo", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """The loaded library.  Raises if it has not been built (call
+    ``paper_2607_14054_gb300.build.build()`` / ``__graft_entry__.build()``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if build_if_missing:
+                _build.build()
+            else:
+                raise RuntimeError(f"CUDA library not built: {path} is missing; run "
+                                   "paper_2607_14054_gb300.build.build() first")
+        lib = ctypes.CDLL(path)
+        vp, i32, i64, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+        tp = ctypes.POINTER(sos_tuning)
+        lib.sos_abi_version.argtypes = []
+        lib.sos_abi_version.restype = i32
+        lib.sos_status_str.argtypes = [ctypes.c_int]
+        lib.sos_status_str.restype = ctypes.c_char_p
+        lib.sos_workspace_size.argtypes = [i32, i32, vp, tp]
+        lib.sos_workspace_size.restype = sz
+        lib.sos_workspace_init.argtypes = [vp, sz, vp]
+        lib.sos_workspace_init.restype = ctypes.c_int
+        lib.sos_filter.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, sz, tp, vp]
+        lib.sos_filter.restype = ctypes.c_int
+        lib.sos_prepare.argtypes = [vp, vp, i32, i32, vp, vp, vp, sz, tp, vp]
+        lib.sos_prepare.restype = ctypes.c_int
+        lib.sos_apply.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
+        lib.sos_apply.restype = ctypes.c_int
+        lib.sos_device_status.argtypes = [vp, vp]
+        lib.sos_device_status.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def _tuning(t):
+    if t is None:
+        return None
+    if isinstance(t, sos_tuning):
+        return ctypes.byref(t)
+    n, w, a, f = (list(t) + [0, 0, 0, 0])[:4]
+    return ctypes.byref(sos_tuning(int(n), int(w), int(a), int(f)))
+
+
+def sos_workspace_size(n_channels: int, kmax: int, lengths_host_ptr: int, tuning=None) -> int:
+    return int(load().sos_workspace_size(n_channels, kmax, ctypes.c_void_p(lengths_host_ptr),
+                                         _tuning(tuning)))
+
+
+def sos_workspace_init(ws_ptr: int, ws_bytes: int, stream: int) -> int:
+    return int(load().sos_workspace_init(ctypes.c_void_p(ws_ptr), ws_bytes, ctypes.c_void_p(stream)))
+
+
+def sos_filter(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y, zf, ws, ws_bytes,
+               tuning, stream) -> int:
+    """All pointer arguments are integers (0 for NULL)."""
+    V = ctypes.c_void_p
+    return int(load().sos_filter(V(x), V(sos), V(K), n_channels, kmax, V(lengths), V(lengths_host),
+                                 V(zi or None), V(y), V(zf or None), V(ws), ws_bytes,
+                                 _tuning(tuning), V(stream)))
+
+
+def sos_prepare(sos, K, n_channels, kmax, lengths, lengths_host, ws, ws_bytes, tuning,
+                stream) -> int:
+    V = ctypes.c_void_p
+    return int(load().sos_prepare(V(sos), V(K), n_channels, kmax, V(lengths), V(lengths_host),
+                                  V(ws), ws_bytes, _tuning(tuning), V(stream)))
+
+
+def sos_apply(x, n_channels, kmax, lengths_host, zi, y, zf, ws, ws_bytes, tuning, stream) -> int:
+    V = ctypes.c_void_p
+    return int(load().sos_apply(V(x), n_channels, kmax, V(lengths_host), V(zi or None), V(y),
+                                V(zf or None), V(ws), ws_bytes, _tuning(tuning), V(stream)))
+
+
+def sos_device_status(ws_ptr: int, stream: int) -> int:
+    return int(load().sos_device_status(ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream)))
+
+
+def sos_status_str(status: int) -> str:
+    return load().sos_status_str(status).decode()
+
+
+def sos_abi_version() -> int:
+    return int(load().sos_abi_version())

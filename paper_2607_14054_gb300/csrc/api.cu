@@ -1,0 +1,230 @@
+// C ABI of the library (declared in include/sosfilt.h): argument checks,
+// workspace carving and the two launches of one call (plan, forward).
+#include <cstring>
+#include <vector>
+
+#include "sos_common.cuh"
+
+namespace sosf {
+cudaError_t launch_plan(const Params& p, cudaStream_t stream);
+cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream);
+bool forward_supported(int N, int W);
+}  // namespace sosf
+
+using namespace sosf;
+
+namespace {
+
+constexpr int32_t kAbiVersion = 1;
+
+struct Tune {
+    int N, W, algo, flags;
+};
+
+bool resolve_tuning(const sos_tuning* t, Tune* out) {
+    Tune r{32, 8, 1, 0};
+    if (t) {
+        if (t->n_blocks) r.N = t->n_blocks;
+        if (t->warps) r.W = t->warps;
+        if (t->algo) r.algo = t->algo;
+        r.flags = t->flags;
+    }
+    if (r.algo != 1) return false;
+    if (!forward_supported(r.N, r.W)) return false;
+    *out = r;
+    return true;
+}
+
+int64_t count_tiles(int32_t C, const int64_t* lengths_host, int64_t T, bool* ok) {
+    int64_t total = 0;
+    *ok = true;
+    for (int32_t c = 0; c < C; ++c) {
+        const int64_t n = lengths_host[c];
+        if (n < 0) {
+            *ok = false;
+            return 0;
+        }
+        total += (n + T - 1) / T;
+    }
+    return total;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t sos_abi_version(void) { return kAbiVersion; }
+
+const char* sos_status_str(sos_status s) {
+    switch (s) {
+        case SOS_OK: return "SOS_OK";
+        case SOS_ERR_ARG: return "SOS_ERR_ARG";
+        case SOS_ERR_UNSTABLE: return "SOS_ERR_UNSTABLE";
+        case SOS_ERR_CUDA: return "SOS_ERR_CUDA";
+        case SOS_ERR_TIMEOUT: return "SOS_ERR_TIMEOUT";
+        case SOS_ERR_WORKSPACE: return "SOS_ERR_WORKSPACE";
+        case SOS_ERR_UNSUPPORTED: return "SOS_ERR_UNSUPPORTED";
+        case SOS_ERR_COEF: return "SOS_ERR_COEF";
+    }
+    return "SOS_ERR_UNKNOWN";
+}
+
+size_t sos_workspace_size(int32_t n_channels, int32_t kmax, const int64_t* lengths_host,
+                          const sos_tuning* tuning) {
+    Tune tu;
+    if (n_channels < 1 || kmax < 1 || kmax > kMaxSections || !lengths_host) return 0;
+    if (!resolve_tuning(tuning, &tu)) return 0;
+    bool ok = true;
+    const int64_t tiles = count_tiles(n_channels, lengths_host, (int64_t)tu.W * kLanes * tu.N, &ok);
+    if (!ok) return 0;
+    return ws_layout(n_channels, kmax, tiles).total;
+}
+
+sos_status sos_workspace_init(void* workspace, size_t ws_bytes, void* stream) {
+    if (!workspace || ws_bytes < sizeof(WsHeader)) return SOS_ERR_ARG;
+    if (cudaMemsetAsync(workspace, 0, ws_bytes, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Validates the shared arguments and fills the workspace part of Params.
+sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, void* workspace,
+                 size_t ws_bytes, const sos_tuning* tuning, Params* p, int64_t* tiles_out,
+                 int64_t* total_len_out) {
+    if (!lengths_host || !workspace) return SOS_ERR_ARG;
+    if (n_channels < 1 || kmax < 1) return SOS_ERR_ARG;
+    if (kmax > kMaxSections) return SOS_ERR_UNSUPPORTED;
+    Tune tu;
+    if (!resolve_tuning(tuning, &tu)) return SOS_ERR_UNSUPPORTED;
+    bool ok = true;
+    const int64_t T = (int64_t)tu.W * kLanes * tu.N;
+    const int64_t tiles = count_tiles(n_channels, lengths_host, T, &ok);
+    if (!ok) return SOS_ERR_ARG;
+    int64_t total_len = 0;
+    for (int32_t c = 0; c < n_channels; ++c) total_len += lengths_host[c];
+    const WsLayout L = ws_layout(n_channels, kmax, tiles);
+    if (ws_bytes < L.total) return SOS_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    p->hdr = reinterpret_cast<WsHeader*>(ws + L.hdr);
+    p->chan = reinterpret_cast<ChanInfo*>(ws + L.chan);
+    p->tb = reinterpret_cast<int64_t*>(ws + L.tb);
+    p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
+    p->c64 = reinterpret_cast<Coef64*>(ws + L.c64);
+    p->flags = reinterpret_cast<uint32_t*>(ws + L.flags);
+    p->agg = reinterpret_cast<double2*>(ws + L.agg);
+    p->inc = reinterpret_cast<double2*>(ws + L.inc);
+    p->cap_tiles = tiles;
+    p->C = n_channels;
+    p->kmax = kmax;
+    p->N = tu.N;
+    p->W = tu.W;
+    p->flags_opt = tu.flags;
+    *tiles_out = tiles;
+    *total_len_out = total_len;
+    return SOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sos_status sos_prepare(const double* sos, const int32_t* K, int32_t n_channels, int32_t kmax,
+                       const int64_t* lengths, const int64_t* lengths_host, void* workspace,
+                       size_t ws_bytes, const sos_tuning* tuning, void* stream) {
+    if (!sos || !K || !lengths) return SOS_ERR_ARG;
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    const sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p,
+                               &tiles, &total);
+    if (s != SOS_OK) return s;
+    p.sos = sos;
+    p.K = K;
+    p.lengths = lengths;
+    if (launch_plan(p, static_cast<cudaStream_t>(stream)) != cudaSuccess) return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
+sos_status sos_apply(const float* x, int32_t n_channels, int32_t kmax,
+                     const int64_t* lengths_host, const float* zi, float* y, float* zf,
+                     void* workspace, size_t ws_bytes, const sos_tuning* tuning, void* stream) {
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    const sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p,
+                               &tiles, &total);
+    if (s != SOS_OK) return s;
+    if (total > 0 && (!x || !y)) return SOS_ERR_ARG;
+    if (x && y && total > 0) {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t bytes = sizeof(float) * (size_t)total;
+        if (xb < yb + bytes && yb < xb + bytes) return SOS_ERR_ARG;  // no overlap
+    }
+    p.x = x;
+    p.y = y;
+    p.zi = zi;
+    p.zf = zf;
+    // at least one CTA so that final states of empty channels get written
+    const int64_t launch_tiles = tiles > 0 ? tiles : 1;
+    if (launch_forward(p, launch_tiles, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
+sos_status sos_filter(const float* x, const double* sos, const int32_t* K, int32_t n_channels,
+                      int32_t kmax, const int64_t* lengths, const int64_t* lengths_host,
+                      const float* zi, float* y, float* zf, void* workspace, size_t ws_bytes,
+                      const sos_tuning* tuning, void* stream) {
+    // check everything the second half checks before enqueuing the first
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p, &tiles,
+                         &total);
+    if (s != SOS_OK) return s;
+    if (!sos || !K || !lengths) return SOS_ERR_ARG;
+    if (total > 0 && (!x || !y)) return SOS_ERR_ARG;
+    if (x && y && total > 0) {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t bytes = sizeof(float) * (size_t)total;
+        if (xb < yb + bytes && yb < xb + bytes) return SOS_ERR_ARG;
+    }
+    s = sos_prepare(sos, K, n_channels, kmax, lengths, lengths_host, workspace, ws_bytes, tuning,
+                    stream);
+    if (s != SOS_OK) return s;
+    return sos_apply(x, n_channels, kmax, lengths_host, zi, y, zf, workspace, ws_bytes, tuning,
+                     stream);
+}
+
+sos_status sos_device_status(void* workspace, void* stream) {
+    if (!workspace) return SOS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SOS_ERR_CUDA;
+    WsHeader h;
+    if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    int32_t result = h.status;
+    if (result == 0 && h.nchan > 0) {
+        // channel table sits right after the header (see ws_layout)
+        const WsLayout L = ws_layout(h.nchan, 1, 1);
+        std::vector<ChanInfo> ch((size_t)h.nchan);
+        if (cudaMemcpy(ch.data(), static_cast<char*>(workspace) + L.chan,
+                       sizeof(ChanInfo) * ch.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return SOS_ERR_CUDA;
+        for (const auto& ci : ch)
+            if (ci.err) {
+                result = ci.err;
+                break;
+            }
+    }
+    const int32_t zero = 0;
+    if (cudaMemcpy(&static_cast<WsHeader*>(workspace)->status, &zero, sizeof(zero),
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    return static_cast<sos_status>(result);
+}
+
+}  // extern "C"

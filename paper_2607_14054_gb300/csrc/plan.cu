@@ -1,0 +1,238 @@
+// Plan kernel: per-call set-up of the workspace, entirely on the device so
+// that a call never synchronises and can be captured into a CUDA graph.
+//
+//  * block C (the last one): channel offsets and tile prefix (exclusive scans
+//    of the lengths) and the status word;
+//  * block c < C: the coefficient tables of channel c, one warp per section.
+//
+// Coefficient tables (paper Sec. VI-B, "pre-computed before filtering"):
+// the rows are normalised by a0; when every b0 of the channel is nonzero the
+// common factor prod_k b0_k is split off (Sec. II, Eq. simple_second_order)
+// and section k's state is carried scaled by 1/G_k, G_k = b0_1 ... b0_k.
+// The DF2T transition A = [[-a1, 1], [-a2, 0]] is raised to the lane step
+// Phi = A^N, the warp step Psi = A^(NL) and the tile step Theta = A^T by
+// repeated squaring in FP64 (one lane, sequential: a few dozen FP64 FMAs),
+// then the per-lane tables Phi^l and Psi^w by binary powering in FP64, each
+// lane forming its own entry.  Only the look-back matrices stay FP64.
+#include <cfloat>
+#include <cmath>
+
+#include "sos_common.cuh"
+
+namespace sosf {
+
+struct M2 {
+    double a, b, c, d;
+};
+
+__device__ __forceinline__ M2 mmul(const M2& x, const M2& y) {
+    return M2{fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d),
+              fma(x.c, y.a, x.d * y.c), fma(x.c, y.b, x.d * y.d)};
+}
+
+__device__ __forceinline__ M2 msq(const M2& x) { return mmul(x, x); }
+
+__device__ __forceinline__ float4 to_f4(const M2& m) {
+    return make_float4((float)m.a, (float)m.b, (float)m.c, (float)m.d);
+}
+
+__device__ __forceinline__ bool finite_row(const double* r) {
+    for (int i = 0; i < 6; ++i)
+        if (!isfinite(r[i])) return false;
+    return true;
+}
+
+// Blocks 0..C-1: coefficients.  Block C: channel table.  256 threads.
+__global__ void __launch_bounds__(256) plan_kernel(Params p) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int C = p.C, kmax = p.kmax;
+
+    if ((int)blockIdx.x == C) {
+        // ---- channel table: exclusive scans of lengths and tile counts ----
+        const int64_t T = (int64_t)p.W * kLanes * p.N;
+        __shared__ int64_t s_wsum_len[8], s_wsum_til[8];
+        __shared__ int64_t s_carry_len, s_carry_til;
+        if (tid == 0) {
+            s_carry_len = 0;
+            s_carry_til = 0;
+            p.hdr->status = 0;
+            p.hdr->nchan = C;
+        }
+        __syncthreads();
+        for (int base = 0; base < C; base += 256) {
+            const int c = base + tid;
+            int64_t len = 0, nt = 0;
+            int32_t K = 0;
+            if (c < C) {
+                len = p.lengths[c];
+                K = p.K[c];
+                if (len < 0 || K < 0 || K > kmax) {
+                    set_status(p.hdr, SOS_ERR_ARG);
+                    len = 0;
+                    K = 0;
+                }
+                nt = len > 0 ? (len + T - 1) / T : 0;
+            }
+            // inclusive warp scans
+            int64_t il = len, it = nt;
+            for (int d = 1; d < 32; d <<= 1) {
+                const int64_t ol = __shfl_up_sync(0xffffffffu, il, d);
+                const int64_t ot = __shfl_up_sync(0xffffffffu, it, d);
+                if (lane >= d) {
+                    il += ol;
+                    it += ot;
+                }
+            }
+            if (lane == 31) {
+                s_wsum_len[warp] = il;
+                s_wsum_til[warp] = it;
+            }
+            __syncthreads();
+            int64_t wl = 0, wt = 0;
+            for (int w = 0; w < warp; ++w) {
+                wl += s_wsum_len[w];
+                wt += s_wsum_til[w];
+            }
+            const int64_t cl = s_carry_len, ct = s_carry_til;
+            if (c < C) {
+                // mode and err belong to the coefficient block of channel c
+                p.chan[c].off = cl + wl + il - len;
+                p.chan[c].len = len;
+                p.chan[c].K = K;
+                p.chan[c].ntiles = (int32_t)nt;
+                p.tb[c] = ct + wt + it - nt;
+            }
+            __syncthreads();
+            if (tid == 255) {
+                s_carry_len = cl + wl + il;
+                s_carry_til = ct + wt + it;
+            }
+            __syncthreads();
+        }
+        if (tid == 0) {
+            const int64_t total = s_carry_til;
+            p.tb[C] = total;
+            if (total > p.cap_tiles) set_status(p.hdr, SOS_ERR_WORKSPACE);
+            p.hdr->total_tiles = total > p.cap_tiles ? 0 : total;
+        }
+        return;
+    }
+
+    // ---- coefficient tables of channel c ----
+    const int c = blockIdx.x;
+    __shared__ double s_b0[kMaxSections];
+    __shared__ int s_mode;
+    __shared__ double s_G[kMaxSections];
+    __shared__ M2 s_chain[kMaxSections][16];  // phi^(2^j) j<5, psi^(2^r) r<4, theta, theta32
+
+    if (tid == 0) p.chan[c].err = 0;
+    __syncthreads();
+    const int K = p.K[c];
+    const bool valid_K = (K >= 0 && K <= kmax);
+    const int Kc = valid_K ? K : 0;
+    const int k = warp;
+    double row[6] = {0, 0, 0, 1, 0, 0};
+    bool active = k < Kc;
+    if (active) {
+        const double* r = p.sos + ((int64_t)c * kmax + k) * 6;
+        for (int i = 0; i < 6; ++i) row[i] = r[i];
+        bool ok = finite_row(row) && row[3] != 0.0;
+        if (!ok) {
+            if (lane == 0) atomicCAS(&p.chan[c].err, 0, (int)SOS_ERR_COEF);
+            row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
+        }
+    }
+    const double a0 = row[3];
+    const double b0 = row[0] / a0, b1 = row[1] / a0, b2 = row[2] / a0;
+    const double a1 = row[4] / a0, a2 = row[5] / a0;
+    if (active && (p.flags_opt & SOS_FLAG_CHECK_STABLE)) {
+        // both roots of z^2 + a1 z + a2 strictly inside the unit circle
+        // (Jury: |a2| < 1 and |a1| < 1 + a2)
+        if (!(fabs(a2) < 1.0 && fabs(a1) < 1.0 + a2) && lane == 0)
+            atomicCAS(&p.chan[c].err, 0, (int)SOS_ERR_UNSTABLE);
+    }
+    if (lane == 0 && k < kMaxSections) s_b0[k] = b0;
+    __syncthreads();
+    if (tid == 0) {
+        // factor b0 out of every section when that keeps the scaled signal in
+        // a safe FP32 range: every b0 nonzero and 2^-60 < |G_k| < 2^60
+        int mode = Kc > 0 ? 1 : 0;
+        double G = 1.0;
+        for (int j = 0; j < Kc; ++j) {
+            G *= s_b0[j];
+            if (!(s_b0[j] != 0.0) || !(fabs(G) > 0x1p-60) || !(fabs(G) < 0x1p60)) mode = 0;
+        }
+        G = 1.0;
+        for (int j = 0; j < kMaxSections; ++j) {
+            if (j < Kc && mode) G *= s_b0[j];
+            s_G[j] = mode ? G : 1.0;
+        }
+        s_mode = mode;
+        p.chan[c].mode = mode;
+    }
+    __syncthreads();
+    const int mode = s_mode;
+
+    if (!active) return;
+
+    // ---- FP64 squaring chain (lane 0) ----
+    const int N = p.N, W = p.W;
+    if (lane == 0) {
+        M2 A{-a1, 1.0, -a2, 0.0};
+        M2 P = A;
+        for (int n = 1; n < N; n <<= 1) P = msq(P);  // A^N
+        s_chain[k][0] = P;
+        for (int j = 1; j < 5; ++j) s_chain[k][j] = msq(s_chain[k][j - 1]);  // Phi^(2^j)
+        M2 Q = msq(s_chain[k][4]);  // Psi = Phi^32
+        s_chain[k][5] = Q;
+        for (int r = 1; r < 4; ++r) s_chain[k][5 + r] = msq(s_chain[k][4 + r]);  // Psi^(2^r)
+        M2 Th = s_chain[k][5];
+        for (int w = 1; w < W; w <<= 1) Th = msq(Th);  // Theta = Psi^W
+        s_chain[k][9] = Th;
+        M2 T32 = Th;
+        for (int i = 0; i < 5; ++i) T32 = msq(T32);
+        s_chain[k][10] = T32;
+    }
+    __syncwarp();
+
+    Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
+    // Phi^lane, binary powering in FP64
+    {
+        M2 P{1.0, 0.0, 0.0, 1.0};
+        for (int j = 0; j < 5; ++j)
+            if ((lane >> j) & 1) P = mmul(P, s_chain[k][j]);
+        out32->lane_pow[lane] = to_f4(P);
+    }
+    if (lane < 16) {
+        M2 P{1.0, 0.0, 0.0, 1.0};
+        for (int r = 0; r < 4; ++r)
+            if ((lane >> r) & 1) P = mmul(P, s_chain[k][5 + r]);
+        out32->psi_w[lane] = to_f4(P);
+    }
+    if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);
+    if (lane < 4) out32->psi_pow[lane] = to_f4(s_chain[k][5 + lane]);
+    if (lane == 0) {
+        const double sb = mode ? 1.0 / b0 : 1.0;
+        out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
+        const double G = s_G[k];
+        out32->misc = make_float4((float)b0, (float)G, (float)(1.0 / G), 0.0f);
+        Coef64* o64 = p.c64 + ((int64_t)c * kmax + k);
+        const M2 Th = s_chain[k][9], T32 = s_chain[k][10];
+        o64->theta[0] = Th.a; o64->theta[1] = Th.b; o64->theta[2] = Th.c; o64->theta[3] = Th.d;
+        o64->theta32[0] = T32.a; o64->theta32[1] = T32.b;
+        o64->theta32[2] = T32.c; o64->theta32[3] = T32.d;
+        o64->G = G;
+        o64->Ginv = 1.0 / G;
+        o64->pad[0] = 0.0;
+        o64->pad[1] = 0.0;
+    }
+}
+
+}  // namespace sosf
+
+namespace sosf {
+cudaError_t launch_plan(const Params& p, cudaStream_t stream) {
+    plan_kernel<<<p.C + 1, 256, 0, stream>>>(p);
+    return cudaGetLastError();
+}
+}  // namespace sosf

@@ -1,0 +1,159 @@
+// Shared definitions of the sm_103a cascaded-biquad kernels: workspace
+// layout, per-section coefficient tables, and small PTX helpers.
+//
+// Notation follows the paper: L = 32 lanes (the block size, Sec. IV, "the
+// warp width on a GPU"), N samples per lane per group (the number of blocks,
+// Sec. V), a group of N*L samples per warp, W warps per tile.  Lane l of a
+// warp holds samples [l*N, l*N + N) of its group in registers v[0..N), so
+// register m of all lanes is the paper's strided block x_m (Sec. V,
+// Eq. recursive_equation_multi_block_form) and the stride-N permutation of
+// Sec. VII-A is the shared-memory transpose done on load.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sosfilt.h"
+
+namespace sosf {
+
+constexpr int kLanes = 32;
+constexpr int kMaxSections = SOS_MAX_SECTIONS;
+constexpr uint32_t kFlagAgg = 1;   // tile aggregate of one section published
+constexpr uint32_t kFlagInc = 2;   // tile inclusive state (outgoing state) published
+constexpr uint32_t kSpinLimit = 1u << 21;
+
+// ---------------------------------------------------------------------------
+// workspace
+// ---------------------------------------------------------------------------
+
+struct WsHeader {
+    uint32_t epoch;         // bumped by the plan kernel once per call
+    uint32_t tile_counter;  // in-order tile dispatch
+    int32_t status;         // device-side status of the latest call (sos_status)
+    uint32_t pad0;
+    int64_t total_tiles;    // tiles of the latest call (device view)
+    int32_t nchan;          // channels of the latest call
+    uint32_t done;          // CTAs of the running filter launch that have finished
+    int64_t pad1[4];
+};
+static_assert(sizeof(WsHeader) == 64, "header size");
+
+struct ChanInfo {
+    int64_t off;     // first sample of the channel in the packed arrays
+    int64_t len;     // samples
+    int32_t K;       // sections used
+    int32_t mode;    // 1: b0 factored out of every section (Sec. II, Eq. simple_second_order)
+    int32_t ntiles;  // tiles of this channel
+    int32_t err;     // coefficient error found by the plan kernel (sos_status), 0 if none
+};
+
+// Per (channel, section) FP32 coefficients and transition-matrix powers.
+// The DF2T state transition of one sample is A = [[-a1, 1], [-a2, 0]];
+// Phi = A^N advances one lane chunk, Psi = A^{N L} one warp group.  All
+// powers are formed in FP64 and rounded once to FP32.  2x2 matrices are
+// stored row-major in a float4 (m00, m01, m10, m11).
+struct __align__(16) Coef32 {
+    float4 ab;            // a1, a2, b1, b2  (b1, b2 divided by b0 when factored)
+    float4 misc;          // b0, G_k (cumulative gain), 1/G_k, unused
+    float4 phi_pow[5];    // Phi^(2^j), j = 0..4 (lane scan)
+    float4 psi_pow[4];    // Psi^(2^r), r = 0..3 (warp scan)
+    float4 psi_w[16];     // Psi^w, w = 0..15 (fold the tile state into warp w)
+    float4 lane_pow[32];  // Phi^l, l = 0..31 (fold the warp state into lane l)
+};
+
+// Per (channel, section) FP64 data for the cross-tile composition.
+struct __align__(16) Coef64 {
+    double theta[4];      // Theta = A^T, T = tile length
+    double theta32[4];    // Theta^32
+    double G;             // cumulative gain through this section (1 if not factored)
+    double Ginv;
+    double pad[2];
+};
+
+struct WsLayout {
+    size_t hdr, chan, tb, c32, c64, flags, agg, inc, total;
+    int64_t cap_tiles;
+};
+
+__host__ __device__ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
+    WsLayout L{};
+    size_t o = 0;
+    L.hdr = o;   o = align_up(o + sizeof(WsHeader), 256);
+    L.chan = o;  o = align_up(o + sizeof(ChanInfo) * (size_t)C, 256);
+    L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
+    L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
+    L.c64 = o;   o = align_up(o + sizeof(Coef64) * (size_t)C * kmax, 256);
+    const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);
+    L.flags = o; o = align_up(o + sizeof(uint32_t) * nt * kmax, 256);
+    L.agg = o;   o = align_up(o + sizeof(double2) * nt * kmax, 256);
+    L.inc = o;   o = align_up(o + sizeof(double2) * nt * kmax, 256);
+    L.total = o;
+    L.cap_tiles = cap_tiles;
+    return L;
+}
+
+// Everything the plan and filter kernels need, by value.
+struct Params {
+    const float* x;
+    float* y;
+    const double* sos;
+    const int32_t* K;
+    const int64_t* lengths;
+    const float* zi;
+    float* zf;
+    WsHeader* hdr;
+    ChanInfo* chan;
+    int64_t* tb;         // tile prefix [C + 1]
+    Coef32* c32;
+    Coef64* c64;
+    uint32_t* flags;     // [kmax][cap_tiles]
+    double2* agg;        // [kmax][cap_tiles]
+    double2* inc;        // [kmax][cap_tiles]
+    int64_t cap_tiles;
+    int32_t C;
+    int32_t kmax;
+    int32_t N;           // samples per lane
+    int32_t W;           // warps per tile
+    int32_t flags_opt;   // SOS_FLAG_*
+    int32_t pad;
+};
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ double2 ld_relaxed_f64x2(const double2* p) {
+    double2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];"
+                 : "=d"(v.x), "=d"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_relaxed_f64x2(double2* p, double2 v) {
+    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y)
+                 : "memory");
+}
+
+__device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
+    return *reinterpret_cast<const volatile int32_t*>(p);
+}
+
+__device__ __forceinline__ void set_status(WsHeader* h, int32_t s) {
+    atomicCAS(&h->status, 0, s);
+}
+
+}  // namespace sosf
