@@ -205,6 +205,36 @@ def run_reference(args):
     return 0
 
 
+def end_to_end(P, x, sos, stream, samples, world, args):
+    """Same metric through the public API with host buffers: pinned host
+    input -> device -> sosfilt -> host output, every step."""
+    import torch
+    xh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
+    xh.copy_(x)
+    yh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
+    xd = torch.empty_like(x)
+    e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        xd.copy_(xh, non_blocking=True)
+        step_e2e_y = P.sosfilt(xd, sos)
+        yh.copy_(step_e2e_y[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        xd.copy_(xh, non_blocking=True)
+        yd, zfd = P.sosfilt(xd, sos)
+        yh.copy_(yd, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    e2e_ms = reduce_max(e2e_ms, world)
+    e2e_value = samples * world / (e2e_ms * 1e-3) / 1e9
+    return e2e_value, e2e_ms
+
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,6 +243,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--tuning", default="", help="N,W (e.g. 32,8)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--clock-seconds", type=float, default=2.0)
     ap.add_argument("--clocks-out", default="")
     args = ap.parse_args()
@@ -278,44 +309,26 @@ def main():
     value = samples * world / (ms_per_step * 1e-3) / 1e9
 
     # sustained loop with clock sampling (same steps, untimed)
-    sampler = ClockSampler(local, args.clocks_out or None)
-    sampler.start()
-    time.sleep(0.3)
-    t0 = time.perf_counter()
-    n_sus = 0
-    while time.perf_counter() - t0 < args.clock_seconds:
-        for _ in range(50):
-            flush.zero_()
-            step()
-            n_sus += 1
-        torch.cuda.synchronize()
-    clocks = sampler.stop()
+    clocks = None
+    if args.clock_seconds > 0:
+        sampler = ClockSampler(local, args.clocks_out or None)
+        sampler.start()
+        time.sleep(0.3)
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < args.clock_seconds:
+            for _ in range(50):
+                flush.zero_()
+                step()
+            torch.cuda.synchronize()
+        clocks = sampler.stop()
 
     # end to end through the public API: pinned host input -> device ->
     # filter -> host output, every step
-    xh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
-    xh.copy_(x)
-    yh = torch.empty(samples, dtype=torch.float32, pin_memory=True)
-    xd = torch.empty_like(x)
-    e_steps = max(3, min(args.steps, 10))
-    for _ in range(2):
-        xd.copy_(xh, non_blocking=True)
-        step_e2e_y = P.sosfilt(xd, sos)
-        yh.copy_(step_e2e_y[0], non_blocking=True)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(e_steps):
-        xd.copy_(xh, non_blocking=True)
-        yd, zfd = P.sosfilt(xd, sos)
-        yh.copy_(yd, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e_steps
-    e2e_ms = reduce_max(e2e_ms, world)
-    e2e_value = samples * world / (e2e_ms * 1e-3) / 1e9
+    e2e_value, e2e_ms = None, None
+    if not args.no_e2e:
+        e2e_value, e2e_ms = end_to_end(P, x, sos, stream, samples, world, args)
 
+    # quick parity sanity
     # quick parity sanity on a prefix (causal: the first n outputs of the full
     # run equal the oracle on the first n inputs)
     parity = None
@@ -368,9 +381,10 @@ def main():
                      "kernel": "sos_forward_kernel", "flops_per_sample": 2 * fmas,
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz ({src} max clock)"},
-        "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
-                "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
-                "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)"},
+        "e2e": None if e2e_value is None else {
+            "value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
+            "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
+            "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)"},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "parity_rel_l2_prefix": parity,

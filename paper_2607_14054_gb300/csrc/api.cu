@@ -113,10 +113,8 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->chan = reinterpret_cast<ChanInfo*>(ws + L.chan);
     p->tb = reinterpret_cast<int64_t*>(ws + L.tb);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
-    p->c64 = reinterpret_cast<Coef64*>(ws + L.c64);
-    p->flags = reinterpret_cast<uint32_t*>(ws + L.flags);
-    p->agg = reinterpret_cast<double2*>(ws + L.agg);
-    p->inc = reinterpret_cast<double2*>(ws + L.inc);
+    p->cdf = reinterpret_cast<CoefDF*>(ws + L.cdf);
+    p->slots = reinterpret_cast<Slot*>(ws + L.slots);
     p->cap_tiles = tiles;
     p->C = n_channels;
     p->kmax = kmax;

@@ -49,111 +49,176 @@ struct Swz {
     __device__ __forceinline__ static int e(int j) { return (g(j >> 2) << 2) | (j & 3); }
 };
 
-__device__ __forceinline__ double2 compose_horner(const double th[4], double u1, double u2,
-                                                  double c1, double c2) {
-    // Theta * u + c
-    return make_double2(fma(th[0], u1, fma(th[1], u2, c1)), fma(th[2], u1, fma(th[3], u2, c2)));
+__device__ __forceinline__ dfm2 load_theta(const CoefDF* cd, int d) {
+    const float4 r0 = __ldg(&cd->theta_pow[d][0]);
+    const float4 r1 = __ldg(&cd->theta_pow[d][1]);
+    return dfm2{df{r0.x, r0.y}, df{r0.z, r0.w}, df{r1.x, r1.y}, df{r1.z, r1.w}};
+}
+
+// Reads one half (inc or agg) of a slot; true if all four words carry `tag`.
+__device__ __forceinline__ bool read_state(const unsigned long long* w, uint32_t tag, df& z1,
+                                           df& z2) {
+    unsigned long long w0, w1, w2, w3;
+    ld_relaxed_v2u64(w, w0, w1);
+    ld_relaxed_v2u64(w + 2, w2, w3);
+    z1 = df{word_value(w0), word_value(w1)};
+    z2 = df{word_value(w2), word_value(w3)};
+    return word_has(w0, tag) && word_has(w1, tag) && word_has(w2, tag) && word_has(w3, tag);
+}
+
+__device__ __forceinline__ void write_state(unsigned long long* w, uint32_t tag, df z1, df z2) {
+    st_relaxed_v2u64(w, tag_word(z1.hi, tag), tag_word(z1.lo, tag));
+    st_relaxed_v2u64(w + 2, tag_word(z2.hi, tag), tag_word(z2.lo, tag));
+}
+
+__device__ __forceinline__ df shfl_df(df v, int src) {
+    return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+}
+
+__device__ __forceinline__ df shfl_xor_df(df v, int m) {
+    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
 }
 
 // Incoming DF2T state of tile t (global index), section k, whose channel-local
 // index is ti >= 1.  Run by one full warp; every lane returns the same value.
-// Predecessor tiles publish either their aggregate c (zero-state outgoing
-// state) or their inclusive value P (true outgoing state); the state entering
-// tile t is Z_t = sum_{i<f} Theta^i c_{t-1-i} + Theta^f P_{t-1-f}, formed by
-// Horner's rule from the nearest inclusive predecessor f.  Windows of 32
-// aggregates without an inclusive value are folded with Theta^32.
-__device__ double2 lookback(const Params& p, int64_t t, int64_t ti, int k, uint32_t epoch,
-                            const Coef64* cc) {
+// Predecessor tiles publish their aggregate c (zero-state outgoing state) and,
+// once known, their inclusive value P (true outgoing state).  The state
+// entering tile t is Z_t = sum_{i<f} Theta^i c_{t-1-i} + Theta^f P_{t-1-f},
+// f the nearest predecessor with an inclusive value; lane i forms its term
+// with the precomputed Theta^i and the warp adds them up.  A window of 32
+// aggregates without an inclusive value is folded with Theta^32 and the walk
+// continues further back.  All of it in double-float.
+__device__ __noinline__ void lookback(const Params& p, int64_t t, int64_t ti, int k, uint32_t epoch,
+                         const CoefDF* cd, df& Z1, df& Z2) {
     const int lane = threadIdx.x & 31;
-    double th[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) th[i] = cc->theta[i];
-    double acc1 = 0.0, acc2 = 0.0;
-    double M[4] = {1.0, 0.0, 0.0, 1.0};
+    const uint32_t tag_inc = (epoch << 2) | kFlagInc, tag_agg = (epoch << 2) | kFlagAgg;
+    const Slot* sl = p.slots + (int64_t)k * p.cap_tiles;
+    // common case: the previous tile already published its inclusive value
+    {
+        df z1, z2;
+        const bool ok = read_state(sl[t - 1].inc, tag_inc, z1, z2);
+        if (__all_sync(0xffffffffu, ok)) {
+            Z1 = z1;
+            Z2 = z2;
+            return;
+        }
+    }
+    df acc1 = df{0.f, 0.f}, acc2 = df{0.f, 0.f};
+    dfm2 M = dfm_identity();
     int64_t base = t - 1;
     int64_t remaining = ti;
-    const uint32_t* fl = p.flags + (int64_t)k * p.cap_tiles;
-    const double2* ag = p.agg + (int64_t)k * p.cap_tiles;
-    const double2* ic = p.inc + (int64_t)k * p.cap_tiles;
+    const dfm2 Ti = load_theta(cd, lane);
     for (;;) {
         const int cnt = (int)(remaining < 32 ? remaining : 32);
         const int64_t j = base - lane;
         const bool valid = lane < cnt;
         uint32_t incm = 0;
         int first = 32;
+        df v1 = df{0.f, 0.f}, v2 = df{0.f, 0.f};
         uint32_t spins = 0;
         for (;;) {
-            const uint32_t st = valid ? ld_acquire_u32(fl + j) : 0u;
-            const bool ok = valid && (st >> 2) == epoch && (st & 3u) != 0u;
-            const bool isinc = ok && (st & 3u) == kFlagInc;
+            df i1, i2, a1, a2;
+            bool isinc = false, isagg = false;
+            if (valid) {
+                isinc = read_state(sl[j].inc, tag_inc, i1, i2);
+                isagg = read_state(sl[j].agg, tag_agg, a1, a2);
+            }
             incm = __ballot_sync(0xffffffffu, isinc);
-            const uint32_t readym = __ballot_sync(0xffffffffu, ok);
+            const uint32_t readym = __ballot_sync(0xffffffffu, isinc || isagg);
+            bool done = false;
             if (incm) {
                 first = __ffs(incm) - 1;
                 const uint32_t need = first == 0 ? 0u : (0xffffffffu >> (32 - first));
-                if ((readym & need) == need) break;
+                done = (readym & need) == need;
             } else if (cnt == 32 && readym == 0xffffffffu) {
                 first = 32;
+                done = true;
+            }
+            if (done) {
+                if (lane < first) {
+                    v1 = a1;
+                    v2 = a2;
+                } else if (lane == first) {
+                    v1 = i1;
+                    v2 = i2;
+                }
                 break;
             }
             ++spins;
             if (spins > kSpinLimit) {
                 if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
-                return make_double2(0.0, 0.0);
+                Z1 = acc1;
+                Z2 = acc2;
+                return;
             }
-            if ((spins & 63u) == 0u && ld_volatile_i32(&p.hdr->status) != 0)
-                return make_double2(0.0, 0.0);
-            __nanosleep(64);
+            if ((spins & 63u) == 0u && ld_volatile_i32(&p.hdr->status) != 0) {
+                Z1 = acc1;
+                Z2 = acc2;
+                return;
+            }
+            __nanosleep(32);
         }
-        double2 val = make_double2(0.0, 0.0);
-        if (lane < first && valid) val = ld_relaxed_f64x2(ag + j);
-        if (incm && lane == first) val = ld_relaxed_f64x2(ic + j);
-        double u1 = 0.0, u2 = 0.0;
-        int top = 31;
-        if (incm) {
-            u1 = __shfl_sync(0xffffffffu, val.x, first);
-            u2 = __shfl_sync(0xffffffffu, val.y, first);
-            top = first - 1;
-        }
-        for (int i = top; i >= 0; --i) {
-            const double c1 = __shfl_sync(0xffffffffu, val.x, i);
-            const double c2 = __shfl_sync(0xffffffffu, val.y, i);
-            const double2 n = compose_horner(th, u1, u2, c1, c2);
-            u1 = n.x;
-            u2 = n.y;
+        // this window's sum: sum_i Theta^i v_i
+        df u1, u2;
+        if (first == 0) {
+            u1 = shfl_df(v1, 0);
+            u2 = shfl_df(v2, 0);
+        } else {
+            const bool use = lane <= first;  // first == 32: every lane
+            df t1 = df{0.f, 0.f}, t2 = df{0.f, 0.f};
+            if (use) dfm_affine(Ti, v1, v2, df{0.f, 0.f}, df{0.f, 0.f}, t1, t2);
+#pragma unroll
+            for (int m = 16; m >= 1; m >>= 1) {
+                t1 = df_add(t1, shfl_xor_df(t1, m));
+                t2 = df_add(t2, shfl_xor_df(t2, m));
+            }
+            u1 = t1;
+            u2 = t2;
         }
         // Z = acc + M u
-        acc1 = fma(M[0], u1, fma(M[1], u2, acc1));
-        acc2 = fma(M[2], u1, fma(M[3], u2, acc2));
-        if (incm) return make_double2(acc1, acc2);
+        df n1, n2;
+        dfm_affine(M, u1, u2, acc1, acc2, n1, n2);
+        acc1 = n1;
+        acc2 = n2;
+        if (incm) {
+            Z1 = acc1;
+            Z2 = acc2;
+            return;
+        }
         // no inclusive value in this window: go 32 tiles further back
-        const double* t32 = cc->theta32;
-        const double m0 = M[0] * t32[0] + M[1] * t32[2], m1 = M[0] * t32[1] + M[1] * t32[3];
-        const double m2 = M[2] * t32[0] + M[3] * t32[2], m3 = M[2] * t32[1] + M[3] * t32[3];
-        M[0] = m0; M[1] = m1; M[2] = m2; M[3] = m3;
+        M = dfm_mul(M, load_theta(cd, 32));
         base -= 32;
         remaining -= 32;
         if (remaining <= 0) {  // cannot happen: a channel's first tile is always inclusive
             if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
-            return make_double2(acc1, acc2);
+            Z1 = acc1;
+            Z2 = acc2;
+            return;
         }
     }
 }
 
 template <int N, int W>
 struct FwdKernel {
-    static constexpr int kThreads = W * 32;
+    static constexpr int kDataThreads = W * 32;
+    static constexpr int kThreads = (W + 1) * 32;  // W data warps + 1 coordinator warp
     static constexpr int kTile = W * 32 * N;
     static constexpr int kGran = kTile / 4;
     static constexpr size_t kSmem = sizeof(float) * kTile;
 };
 
-// One section of the cascade on the register-resident chunk v[0..N).
+// Per-section shared state between the data warps and the coordinator.
+template <int W>
+struct SectionShared {
+    float2 agg[W];  // zero-state state leaving each warp's group
+    float2 win[W];  // true state entering each warp's group
+};
+
+// One section of the cascade on a data warp's register-resident chunk.
 template <int N, int W, bool FACT>
-__device__ __forceinline__ void run_section(const Params& p, float (&v)[N], int k, int c,
-                                            int64_t t, int64_t ti, int64_t nt, uint32_t epoch,
-                                            float2* s_agg, double2* s_Z, bool zf_owner, int mq,
-                                            float* zf_out, float* s_own) {
+__device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int k, int c,
+                                             SectionShared<W>* sh, bool zf_owner, int mq,
+                                             float* s_own) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const Coef32* cf = p.c32 + ((int64_t)c * p.kmax + k);
     const float4 ab = __ldg(&cf->ab);
@@ -210,13 +275,54 @@ __device__ __forceinline__ void run_section(const Params& p, float (&v)[N], int 
         E1 = 0.f;
         E2 = 0.f;
     }
-    if (lane == 31) s_agg[warp] = make_float2(S1, S2);
-    __syncthreads();
+    if (lane == 31) sh->agg[warp] = make_float2(S1, S2);
+    __syncthreads();  // B1: warp aggregates ready for the coordinator
+    __syncthreads();  // B2: the coordinator has placed this warp's incoming state
+    const float2 Zw = sh->win[warp];
 
-    // S5: scan over the W warp aggregates (every warp redundantly)
+    // fold the warp's true incoming state into this lane's
+    const float4 Pl = __ldg(&cf->lane_pow[lane]);
+    const float zin1 = fmaf(Pl.x, Zw.x, fmaf(Pl.y, Zw.y, E1));
+    const float zin2 = fmaf(Pl.z, Zw.x, fmaf(Pl.w, Zw.y, E2));
+
+    // S4 (iii): re-run the recursion from the true incoming state
+    v[0] = v[0] + zin1;
+    v[1] = fmaf(-a1, v[0], v[1] + zin2);
+#pragma unroll
+    for (int m = 2; m < N; ++m) v[m] = fmaf(-a1, v[m - 1], fmaf(-a2, v[m - 2], v[m]));
+
+    // S8: final state at the channel's last sample
+    if (zf_owner) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) s_own[m] = v[m];
+        const float yq = s_own[mq];
+        const float yqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
+        float f1;
+        if (mq >= 1) {
+            f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
+        } else {
+            f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
+        }
+        const float f2 = fmaf(b2, xq, -a2 * yq);
+        const float G = FACT ? __ldg(&cf->misc).y : 1.0f;
+        p.zf[((int64_t)c * p.kmax + k) * 2 + 0] = f1 * G;
+        p.zf[((int64_t)c * p.kmax + k) * 2 + 1] = f2 * G;
+    }
+}
+
+// The coordinator warp's part of one section (S5): scan over the W warp
+// aggregates, publication of the tile's aggregate, look-back for the tile's
+// incoming state, publication of its outgoing state, and each warp's
+// incoming state.
+template <int W>
+__device__ __forceinline__ void coord_section(const Params& p, int k, int c, int64_t t, int64_t ti,
+                                              int64_t nt, uint32_t epoch, SectionShared<W>* sh) {
+    const int lane = threadIdx.x & 31;
+    const Coef32* cf = p.c32 + ((int64_t)c * p.kmax + k);
+    __syncthreads();  // B1
     float A1 = 0.f, A2 = 0.f;
     if (lane < W) {
-        const float2 a = s_agg[lane];
+        const float2 a = sh->agg[lane];
         A1 = a.x;
         A2 = a.y;
     }
@@ -231,90 +337,59 @@ __device__ __forceinline__ void run_section(const Params& p, float (&v)[N], int 
             A2 = fmaf(P.z, t1, fmaf(P.w, t2, A2));
         }
     }
-    // zero-state state entering this warp (exclusive) and leaving the tile
-    float WE1 = __shfl_sync(0xffffffffu, A1, warp > 0 ? warp - 1 : 0);
-    float WE2 = __shfl_sync(0xffffffffu, A2, warp > 0 ? warp - 1 : 0);
-    if (warp == 0) {
+    float WE1 = __shfl_up_sync(0xffffffffu, A1, 1);
+    float WE2 = __shfl_up_sync(0xffffffffu, A2, 1);
+    if (lane == 0) {
         WE1 = 0.f;
         WE2 = 0.f;
     }
-
-    if (warp == 0) {
-        const float C1 = __shfl_sync(0xffffffffu, A1, W - 1);
-        const float C2 = __shfl_sync(0xffffffffu, A2, W - 1);
-        const Coef64* cc = p.c64 + ((int64_t)c * p.kmax + k);
-        const bool has_succ = ti + 1 < nt;
-        const size_t slot = (size_t)k * p.cap_tiles + (size_t)t;
-        double2 Z;
-        if (ti == 0) {
-            Z = make_double2(0.0, 0.0);
-            if (p.zi) {
-                const double gi = cc->Ginv;
-                Z.x = (double)p.zi[((int64_t)c * p.kmax + k) * 2 + 0] * gi;
-                Z.y = (double)p.zi[((int64_t)c * p.kmax + k) * 2 + 1] * gi;
-            }
-        } else {
-            if (has_succ && lane == 0) {
-                st_relaxed_f64x2(p.agg + slot, make_double2((double)C1, (double)C2));
-                st_release_u32(p.flags + slot, (epoch << 2) | kFlagAgg);
-            }
-            Z = lookback(p, t, ti, k, epoch, cc);
+    const float C1 = __shfl_sync(0xffffffffu, A1, W - 1);
+    const float C2 = __shfl_sync(0xffffffffu, A2, W - 1);
+    const CoefDF* cd = p.cdf + ((int64_t)c * p.kmax + k);
+    const bool has_succ = ti + 1 < nt;
+    Slot* slot = p.slots + (int64_t)k * p.cap_tiles + t;
+    df Z1, Z2;
+    if (ti == 0) {
+        Z1 = df{0.f, 0.f};
+        Z2 = df{0.f, 0.f};
+        if (p.zi) {
+            const float gi = __ldg(&cf->misc).z;
+            const float* zi = p.zi + ((int64_t)c * p.kmax + k) * 2;
+            // zi / G_k, the exact product split into hi + lo
+            const float q1 = zi[0] * gi, q2 = zi[1] * gi;
+            Z1 = df{q1, fmaf(zi[0], gi, -q1)};
+            Z2 = df{q2, fmaf(zi[1], gi, -q2)};
         }
-        if (has_succ && lane == 0) {
-            const double2 P = compose_horner(cc->theta, Z.x, Z.y, (double)C1, (double)C2);
-            st_relaxed_f64x2(p.inc + slot, P);
-            st_release_u32(p.flags + slot, (epoch << 2) | kFlagInc);
-        }
-        if (lane == 0) *s_Z = Z;
+    } else {
+        if (has_succ && lane == 0)
+            write_state(slot->agg, (epoch << 2) | kFlagAgg, df_from(C1), df_from(C2));
+        lookback(p, t, ti, k, epoch, cd, Z1, Z2);
     }
-    __syncthreads();
-    const double2 Zt = *s_Z;
-
-    // fold: state entering this warp, then this lane
-    const float z1 = (float)Zt.x, z2 = (float)Zt.y;
-    const float4 Pw = __ldg(&cf->psi_w[warp]);
-    const float Zw1 = fmaf(Pw.x, z1, fmaf(Pw.y, z2, WE1));
-    const float Zw2 = fmaf(Pw.z, z1, fmaf(Pw.w, z2, WE2));
-    const float4 Pl = __ldg(&cf->lane_pow[lane]);
-    const float zin1 = fmaf(Pl.x, Zw1, fmaf(Pl.y, Zw2, E1));
-    const float zin2 = fmaf(Pl.z, Zw1, fmaf(Pl.w, Zw2, E2));
-
-    // S4 (iii): re-run the recursion from the true incoming state
-    v[0] = v[0] + zin1;
-    v[1] = fmaf(-a1, v[0], v[1] + zin2);
-#pragma unroll
-    for (int m = 2; m < N; ++m) v[m] = fmaf(-a1, v[m - 1], fmaf(-a2, v[m - 2], v[m]));
-
-    // S8: final state at the channel's last sample
-    if (zf_owner) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s_own[m] = v[m];
-        const float yq = s_own[mq];
-        const float yqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
-        float f1, f2;
-        if (mq >= 1) {
-            f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
-        } else {
-            f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
-        }
-        f2 = fmaf(b2, xq, -a2 * yq);
-        const float G = FACT ? __ldg(&cf->misc).y : 1.0f;
-        zf_out[((int64_t)c * p.kmax + k) * 2 + 0] = f1 * G;
-        zf_out[((int64_t)c * p.kmax + k) * 2 + 1] = f2 * G;
+    if (has_succ && lane == 0) {
+        df P1, P2;
+        dfm_affine(load_theta(cd, 1), Z1, Z2, df_from(C1), df_from(C2), P1, P2);
+        write_state(slot->inc, (epoch << 2) | kFlagInc, P1, P2);
     }
+    if (lane < W) {
+        const float z1 = df_to_float(Z1), z2 = df_to_float(Z2);
+        const float4 Pw = __ldg(&cf->psi_w[lane]);
+        sh->win[lane] = make_float2(fmaf(Pw.x, z1, fmaf(Pw.y, z2, WE1)),
+                                    fmaf(Pw.z, z1, fmaf(Pw.w, z2, WE2)));
+    }
+    __syncthreads();  // B2
 }
 
-template <int N, int W>
-__global__ void __launch_bounds__(W * 32) sos_forward_kernel(Params p) {
+template <int N, int W, int MINB>
+__global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params p) {
     using KT = FwdKernel<N, W>;
     using S = Swz<N>;
     extern __shared__ float4 s_tile4[];
     float* s_tile = reinterpret_cast<float*>(s_tile4);
-    __shared__ float2 s_agg[W];
-    __shared__ double2 s_Z;
+    __shared__ SectionShared<W> sh;
     __shared__ int64_t s_t;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool coord = warp == W;
     const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&p.hdr->epoch);
     const int64_t total = p.hdr->total_tiles;
 
@@ -355,7 +430,8 @@ __global__ void __launch_bounds__(W * 32) sos_forward_kernel(Params p) {
         const int r = (int)(rem < KT::kTile ? rem : KT::kTile);  // valid samples
         const float* src = p.x + ci.off + start;
 
-        // S2: global -> shared (swizzled), zero beyond the channel end
+        // S2: global -> shared (swizzled), zero beyond the channel end; all
+        // W + 1 warps take part
         const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && r == KT::kTile;
         if (vec) {
             const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -366,46 +442,47 @@ __global__ void __launch_bounds__(W * 32) sos_forward_kernel(Params p) {
                 s_tile[S::e(j)] = j < r ? __ldcs(src + j) : 0.0f;
         }
         __syncthreads();
-        float v[N];
-        const int chunk = warp * 32 + lane;
-#pragma unroll
-        for (int g = 0; g < N / 4; ++g) {
-            const float4 q = s_tile4[S::g(chunk * (N / 4) + g)];
-            v[4 * g + 0] = q.x;
-            v[4 * g + 1] = q.y;
-            v[4 * g + 2] = q.z;
-            v[4 * g + 3] = q.w;
-        }
 
-        // owner of the channel's last sample (for zf)
-        const bool last = (ti + 1 == nt);
-        const int q = r - 1;
-        const bool zf_owner = last && p.zf != nullptr && (q / N) == chunk;
-        const int mq = q % N;
-
-        // the owner's scratch: its own chunk of the tile buffer, unused while
-        // the sections run (plain layout, only that lane touches it)
-        float* s_own = s_tile + chunk * N;
-        if (ci.mode) {
-            for (int k = 0; k < ci.K; ++k)
-                run_section<N, W, true>(p, v, k, c, t, ti, nt, epoch, s_agg, &s_Z, zf_owner, mq,
-                                        p.zf, s_own);
-            const float G = __ldg(&p.c32[(int64_t)c * p.kmax + ci.K - 1].misc).y;
-#pragma unroll
-            for (int m = 0; m < N; ++m) v[m] *= G;
+        if (coord) {
+            for (int k = 0; k < ci.K; ++k) coord_section<W>(p, k, c, t, ti, nt, epoch, &sh);
         } else {
-            for (int k = 0; k < ci.K; ++k)
-                run_section<N, W, false>(p, v, k, c, t, ti, nt, epoch, s_agg, &s_Z, zf_owner, mq,
-                                         p.zf, s_own);
-        }
-
-        // S7: registers -> shared (swizzled) -> global
-        __syncwarp();  // order the zf owner's scratch writes before the lanes' stores
+            float v[N];
+            const int chunk = warp * 32 + lane;
 #pragma unroll
-        for (int g = 0; g < N / 4; ++g)
-            s_tile4[S::g(chunk * (N / 4) + g)] =
-                make_float4(v[4 * g + 0], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+            for (int g = 0; g < N / 4; ++g) {
+                const float4 q = s_tile4[S::g(chunk * (N / 4) + g)];
+                v[4 * g + 0] = q.x;
+                v[4 * g + 1] = q.y;
+                v[4 * g + 2] = q.z;
+                v[4 * g + 3] = q.w;
+            }
+            // owner of the channel's last sample (for zf)
+            const bool last = (ti + 1 == nt);
+            const int q = r - 1;
+            const bool zf_owner = last && p.zf != nullptr && (q / N) == chunk;
+            const int mq = q % N;
+            // the owner's scratch: its own chunk of the tile buffer, unused
+            // while the sections run (plain layout, only that lane touches it)
+            float* s_own = s_tile + chunk * N;
+            if (ci.mode) {
+                for (int k = 0; k < ci.K; ++k)
+                    data_section<N, W, true>(p, v, k, c, &sh, zf_owner, mq, s_own);
+                const float G = __ldg(&p.c32[(int64_t)c * p.kmax + ci.K - 1].misc).y;
+#pragma unroll
+                for (int m = 0; m < N; ++m) v[m] *= G;
+            } else {
+                for (int k = 0; k < ci.K; ++k)
+                    data_section<N, W, false>(p, v, k, c, &sh, zf_owner, mq, s_own);
+            }
+            // S7: registers -> shared (swizzled)
+            __syncwarp();  // order the zf owner's scratch writes before the lanes' stores
+#pragma unroll
+            for (int g = 0; g < N / 4; ++g)
+                s_tile4[S::g(chunk * (N / 4) + g)] =
+                    make_float4(v[4 * g + 0], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
+        }
         __syncthreads();
+        // shared -> global, all W + 1 warps
         float* dst = p.y + ci.off + start;
         if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && r == KT::kTile) {
             float4* d4 = reinterpret_cast<float4*>(dst);
@@ -443,12 +520,14 @@ struct KernelEntry {
     size_t smem;
 };
 
-#define SOSF_ENTRY(N_, W_) \
-    {N_, W_, reinterpret_cast<const void*>(&sos_forward_kernel<N_, W_>), FwdKernel<N_, W_>::kSmem}
+// (N, W, minimum resident CTAs per SM the register allocation must allow)
+#define SOSF_ENTRY(N_, W_, B_)                                                              \
+    {N_, W_, reinterpret_cast<const void*>(&sos_forward_kernel<N_, W_, B_>),              \
+     FwdKernel<N_, W_>::kSmem}
 
 static const KernelEntry kEntries[] = {
-    SOSF_ENTRY(16, 8), SOSF_ENTRY(16, 16), SOSF_ENTRY(32, 4), SOSF_ENTRY(32, 8),
-    SOSF_ENTRY(32, 16), SOSF_ENTRY(64, 4), SOSF_ENTRY(64, 8),
+    SOSF_ENTRY(16, 8, 3), SOSF_ENTRY(16, 16, 2), SOSF_ENTRY(32, 4, 4), SOSF_ENTRY(32, 8, 2),
+    SOSF_ENTRY(32, 16, 1), SOSF_ENTRY(64, 4, 2), SOSF_ENTRY(64, 8, 1),
 };
 
 bool forward_supported(int N, int W) {
@@ -480,7 +559,7 @@ cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t str
             if (err != cudaSuccess) return err;
         }
         int occ = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->fn, p.W * 32, ke->smem);
+        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->fn, (p.W + 1) * 32, ke->smem);
         if (err != cudaSuccess) return err;
         s_occ[dev][idx] = occ > 0 ? occ : 1;
     }
@@ -488,7 +567,8 @@ cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t str
     if (host_tiles < grid) grid = host_tiles;
     if (grid < 1) return cudaSuccess;
     void* args[] = {const_cast<Params*>(&p)};
-    return cudaLaunchKernel(ke->fn, dim3((unsigned)grid), dim3(p.W * 32), args, ke->smem, stream);
+    return cudaLaunchKernel(ke->fn, dim3((unsigned)grid), dim3((p.W + 1) * 32), args, ke->smem,
+                            stream);
 }
 
 }  // namespace sosf

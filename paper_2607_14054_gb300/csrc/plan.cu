@@ -11,9 +11,12 @@
 // and section k's state is carried scaled by 1/G_k, G_k = b0_1 ... b0_k.
 // The DF2T transition A = [[-a1, 1], [-a2, 0]] is raised to the lane step
 // Phi = A^N, the warp step Psi = A^(NL) and the tile step Theta = A^T by
-// repeated squaring in FP64 (one lane, sequential: a few dozen FP64 FMAs),
-// then the per-lane tables Phi^l and Psi^w by binary powering in FP64, each
-// lane forming its own entry.  Only the look-back matrices stay FP64.
+// repeated squaring, then the per-lane tables Phi^l, Psi^w and Theta^d by
+// binary powering, each lane forming its own entry.  All of it runs in
+// double-float arithmetic (about 48 significand bits) on the FP32 pipe:
+// GB300's FP64 FMA is 1/64 of its FP32 rate with a 64-cycle latency.  The
+// per-sample tables are rounded once to FP32; the Theta^d used by the
+// cross-tile look-back stay double-float.
 #include <cfloat>
 #include <cmath>
 
@@ -21,19 +24,13 @@
 
 namespace sosf {
 
-struct M2 {
-    double a, b, c, d;
-};
-
-__device__ __forceinline__ M2 mmul(const M2& x, const M2& y) {
-    return M2{fma(x.a, y.a, x.b * y.c), fma(x.a, y.b, x.b * y.d),
-              fma(x.c, y.a, x.d * y.c), fma(x.c, y.b, x.d * y.d)};
+__device__ __forceinline__ df df_of_double(double v) {
+    const float hi = (float)v;
+    return df{hi, (float)(v - (double)hi)};
 }
 
-__device__ __forceinline__ M2 msq(const M2& x) { return mmul(x, x); }
-
-__device__ __forceinline__ float4 to_f4(const M2& m) {
-    return make_float4((float)m.a, (float)m.b, (float)m.c, (float)m.d);
+__device__ __forceinline__ float4 to_f4(const dfm2& m) {
+    return make_float4(df_to_float(m.a), df_to_float(m.b), df_to_float(m.c), df_to_float(m.d));
 }
 
 __device__ __forceinline__ bool finite_row(const double* r) {
@@ -123,7 +120,8 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     __shared__ double s_b0[kMaxSections];
     __shared__ int s_mode;
     __shared__ double s_G[kMaxSections];
-    __shared__ M2 s_chain[kMaxSections][16];  // phi^(2^j) j<5, psi^(2^r) r<4, theta, theta32
+    // Phi^(2^j) j<5, Psi^(2^r) r<4, Theta^(2^i) i<6
+    __shared__ dfm2 s_chain[kMaxSections][15];
 
     if (tid == 0) p.chan[c].err = 0;
     __syncthreads();
@@ -142,9 +140,9 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
             row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
         }
     }
-    const double a0 = row[3];
-    const double b0 = row[0] / a0, b1 = row[1] / a0, b2 = row[2] / a0;
-    const double a1 = row[4] / a0, a2 = row[5] / a0;
+    const double ia0 = 1.0 / row[3];
+    const double b0 = row[0] * ia0, b1 = row[1] * ia0, b2 = row[2] * ia0;
+    const double a1 = row[4] * ia0, a2 = row[5] * ia0;
     if (active && (p.flags_opt & SOS_FLAG_CHECK_STABLE)) {
         // both roots of z^2 + a1 z + a2 strictly inside the unit circle
         // (Jury: |a2| < 1 and |a1| < 1 + a2)
@@ -175,38 +173,46 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
 
     if (!active) return;
 
-    // ---- FP64 squaring chain (lane 0) ----
+    // ---- double-float squaring chain (lane 0) ----
     const int N = p.N, W = p.W;
     if (lane == 0) {
-        M2 A{-a1, 1.0, -a2, 0.0};
-        M2 P = A;
-        for (int n = 1; n < N; n <<= 1) P = msq(P);  // A^N
+        const dfm2 A{df_of_double(-a1), df{1.f, 0.f}, df_of_double(-a2), df{0.f, 0.f}};
+        dfm2 P = A;
+        for (int n = 1; n < N; n <<= 1) P = dfm_mul(P, P);  // A^N
         s_chain[k][0] = P;
-        for (int j = 1; j < 5; ++j) s_chain[k][j] = msq(s_chain[k][j - 1]);  // Phi^(2^j)
-        M2 Q = msq(s_chain[k][4]);  // Psi = Phi^32
-        s_chain[k][5] = Q;
-        for (int r = 1; r < 4; ++r) s_chain[k][5 + r] = msq(s_chain[k][4 + r]);  // Psi^(2^r)
-        M2 Th = s_chain[k][5];
-        for (int w = 1; w < W; w <<= 1) Th = msq(Th);  // Theta = Psi^W
+        for (int j = 1; j < 5; ++j) s_chain[k][j] = dfm_mul(s_chain[k][j - 1], s_chain[k][j - 1]);
+        s_chain[k][5] = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
+        for (int r = 1; r < 4; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
+        dfm2 Th = s_chain[k][5];
+        for (int w = 1; w < W; w <<= 1) Th = dfm_mul(Th, Th);  // Theta = Psi^W
         s_chain[k][9] = Th;
-        M2 T32 = Th;
-        for (int i = 0; i < 5; ++i) T32 = msq(T32);
-        s_chain[k][10] = T32;
+        for (int i = 1; i < 6; ++i) s_chain[k][9 + i] = dfm_mul(s_chain[k][8 + i], s_chain[k][8 + i]);
     }
     __syncwarp();
 
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
-    // Phi^lane, binary powering in FP64
+    CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
     {
-        M2 P{1.0, 0.0, 0.0, 1.0};
+        // Phi^lane and Theta^lane by binary powering, each lane its own entry
+        dfm2 P = dfm_identity(), Q = dfm_identity();
         for (int j = 0; j < 5; ++j)
-            if ((lane >> j) & 1) P = mmul(P, s_chain[k][j]);
+            if ((lane >> j) & 1) {
+                P = dfm_mul(P, s_chain[k][j]);
+                Q = dfm_mul(Q, s_chain[k][9 + j]);
+            }
         out32->lane_pow[lane] = to_f4(P);
+        outdf->theta_pow[lane][0] = make_float4(Q.a.hi, Q.a.lo, Q.b.hi, Q.b.lo);
+        outdf->theta_pow[lane][1] = make_float4(Q.c.hi, Q.c.lo, Q.d.hi, Q.d.lo);
+        if (lane == 0) {
+            const dfm2 T32 = s_chain[k][14];
+            outdf->theta_pow[32][0] = make_float4(T32.a.hi, T32.a.lo, T32.b.hi, T32.b.lo);
+            outdf->theta_pow[32][1] = make_float4(T32.c.hi, T32.c.lo, T32.d.hi, T32.d.lo);
+        }
     }
     if (lane < 16) {
-        M2 P{1.0, 0.0, 0.0, 1.0};
+        dfm2 P = dfm_identity();
         for (int r = 0; r < 4; ++r)
-            if ((lane >> r) & 1) P = mmul(P, s_chain[k][5 + r]);
+            if ((lane >> r) & 1) P = dfm_mul(P, s_chain[k][5 + r]);
         out32->psi_w[lane] = to_f4(P);
     }
     if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);
@@ -216,15 +222,6 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
         const double G = s_G[k];
         out32->misc = make_float4((float)b0, (float)G, (float)(1.0 / G), 0.0f);
-        Coef64* o64 = p.c64 + ((int64_t)c * kmax + k);
-        const M2 Th = s_chain[k][9], T32 = s_chain[k][10];
-        o64->theta[0] = Th.a; o64->theta[1] = Th.b; o64->theta[2] = Th.c; o64->theta[3] = Th.d;
-        o64->theta32[0] = T32.a; o64->theta32[1] = T32.b;
-        o64->theta32[2] = T32.c; o64->theta32[3] = T32.d;
-        o64->G = G;
-        o64->Ginv = 1.0 / G;
-        o64->pad[0] = 0.0;
-        o64->pad[1] = 0.0;
     }
 }
 

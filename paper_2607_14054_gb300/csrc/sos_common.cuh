@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/sosfilt.h"
+#include "sos_df.cuh"
 
 namespace sosf {
 
@@ -63,17 +64,25 @@ struct __align__(16) Coef32 {
     float4 lane_pow[32];  // Phi^l, l = 0..31 (fold the warp state into lane l)
 };
 
-// Per (channel, section) FP64 data for the cross-tile composition.
-struct __align__(16) Coef64 {
-    double theta[4];      // Theta = A^T, T = tile length
-    double theta32[4];    // Theta^32
-    double G;             // cumulative gain through this section (1 if not factored)
-    double Ginv;
-    double pad[2];
+// Per (channel, section) double-float powers of the tile transition
+// Theta = A^T (T = tile length) for the cross-tile composition: entry d holds
+// Theta^d, d = 0..32, as (a.hi, a.lo, b.hi, b.lo), (c.hi, c.lo, d.hi, d.lo).
+struct __align__(16) CoefDF {
+    float4 theta_pow[33][2];
+};
+
+// One look-back slot per (section, tile): the tile's inclusive (true
+// outgoing) state and its aggregate (zero-state outgoing) state, each as four
+// 64-bit words (z1.hi, z1.lo, z2.hi, z2.lo).  Every word carries its own tag
+// (epoch << 2 | kind) in the low 32 bits, so a reader validates what it read
+// word by word: one L2 round trip, no separate flag, no fence.
+struct __align__(64) Slot {
+    unsigned long long inc[4];
+    unsigned long long agg[4];
 };
 
 struct WsLayout {
-    size_t hdr, chan, tb, c32, c64, flags, agg, inc, total;
+    size_t hdr, chan, tb, c32, cdf, slots, total;
     int64_t cap_tiles;
 };
 
@@ -86,11 +95,9 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.chan = o;  o = align_up(o + sizeof(ChanInfo) * (size_t)C, 256);
     L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
     L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
-    L.c64 = o;   o = align_up(o + sizeof(Coef64) * (size_t)C * kmax, 256);
+    L.cdf = o;   o = align_up(o + sizeof(CoefDF) * (size_t)C * kmax, 256);
     const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);
-    L.flags = o; o = align_up(o + sizeof(uint32_t) * nt * kmax, 256);
-    L.agg = o;   o = align_up(o + sizeof(double2) * nt * kmax, 256);
-    L.inc = o;   o = align_up(o + sizeof(double2) * nt * kmax, 256);
+    L.slots = o; o = align_up(o + sizeof(Slot) * nt * kmax, 256);
     L.total = o;
     L.cap_tiles = cap_tiles;
     return L;
@@ -109,10 +116,8 @@ struct Params {
     ChanInfo* chan;
     int64_t* tb;         // tile prefix [C + 1]
     Coef32* c32;
-    Coef64* c64;
-    uint32_t* flags;     // [kmax][cap_tiles]
-    double2* agg;        // [kmax][cap_tiles]
-    double2* inc;        // [kmax][cap_tiles]
+    CoefDF* cdf;
+    Slot* slots;         // [kmax][cap_tiles]
     int64_t cap_tiles;
     int32_t C;
     int32_t kmax;
@@ -126,26 +131,26 @@ struct Params {
 // PTX helpers
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ void ld_relaxed_v2u64(const unsigned long long* p, unsigned long long& a,
+                                                 unsigned long long& b) {
+    asm volatile("ld.relaxed.gpu.global.v2.b64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p) : "memory");
 }
 
-__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void st_relaxed_v2u64(unsigned long long* p, unsigned long long a,
+                                                 unsigned long long b) {
+    asm volatile("st.relaxed.gpu.global.v2.b64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 
-__device__ __forceinline__ double2 ld_relaxed_f64x2(const double2* p) {
-    double2 v;
-    asm volatile("ld.relaxed.gpu.global.v2.f64 {%0, %1}, [%2];"
-                 : "=d"(v.x), "=d"(v.y) : "l"(p) : "memory");
-    return v;
+__device__ __forceinline__ unsigned long long tag_word(float v, uint32_t tag) {
+    return ((unsigned long long)__float_as_uint(v) << 32) | tag;
 }
 
-__device__ __forceinline__ void st_relaxed_f64x2(double2* p, double2 v) {
-    asm volatile("st.relaxed.gpu.global.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y)
-                 : "memory");
+__device__ __forceinline__ float word_value(unsigned long long w) {
+    return __uint_as_float((uint32_t)(w >> 32));
+}
+
+__device__ __forceinline__ bool word_has(unsigned long long w, uint32_t tag) {
+    return (uint32_t)w == tag;
 }
 
 __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {

@@ -1,0 +1,78 @@
+// Double-float ("df") arithmetic: a value is an unevaluated sum hi + lo of
+// two FP32 numbers with |lo| <= ulp(hi)/2, giving about 48 significand bits.
+//
+// GB300 executes FP64 FMAs at 1/64 of the FP32 rate with a 64-cycle
+// dependent latency (measured on this part), so every quantity the method
+// keeps beyond FP32 (transition-matrix powers, cross-tile state composition)
+// is carried in df on the FP32 pipe instead.  The building blocks are the
+// error-free transformations of Knuth (TwoSum), Dekker (Fast2Sum) and the
+// FMA-based TwoProduct (see Muller et al., Handbook of Floating-Point
+// Arithmetic, ch. 4 and 14); nvcc does not reassociate FP32 additions, so the
+// sequences stay exact.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace sosf {
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df df_two_sum(float a, float b) {
+    const float s = a + b;
+    const float bb = s - a;
+    const float e = (a - (s - bb)) + (b - bb);
+    return df{s, e};
+}
+
+__device__ __forceinline__ df df_fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+    const float s = a + b;
+    return df{s, b - (s - a)};
+}
+
+__device__ __forceinline__ df df_from(float a) { return df{a, 0.0f}; }
+
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = df_two_sum(a.hi, b.hi);
+    const df t = df_two_sum(a.lo, b.lo);
+    s.lo += t.hi;
+    s = df_fast_two_sum(s.hi, s.lo);
+    s.lo += t.lo;
+    return df_fast_two_sum(s.hi, s.lo);
+}
+
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    return df_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+
+// 2x2 matrix in df, row-major
+struct dfm2 {
+    df a, b, c, d;
+};
+
+__device__ __forceinline__ dfm2 dfm_mul(const dfm2& x, const dfm2& y) {
+    return dfm2{df_add(df_mul(x.a, y.a), df_mul(x.b, y.c)), df_add(df_mul(x.a, y.b), df_mul(x.b, y.d)),
+                df_add(df_mul(x.c, y.a), df_mul(x.d, y.c)), df_add(df_mul(x.c, y.b), df_mul(x.d, y.d))};
+}
+
+__device__ __forceinline__ dfm2 dfm_identity() {
+    return dfm2{df{1.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}, df{1.f, 0.f}};
+}
+
+// y = M u + c
+__device__ __forceinline__ void dfm_affine(const dfm2& M, df u1, df u2, df c1, df c2, df& y1,
+                                           df& y2) {
+    y1 = df_add(df_add(df_mul(M.a, u1), df_mul(M.b, u2)), c1);
+    y2 = df_add(df_add(df_mul(M.c, u1), df_mul(M.d, u2)), c2);
+}
+
+__device__ __forceinline__ float df_to_float(df a) { return a.hi + a.lo; }
+
+}  // namespace sosf

@@ -188,7 +188,7 @@ def test_bandpass16_full_size():
     args = (wl.x, wl.sos, wl.K, wl.lengths, wl.zi)
     y, zf = run_gpu(args)
     y_ref, zf_ref = run_oracle(*args)
-    err = check(y, zf, y_ref, zf_ref, wl.lengths.numpy(), wl.K.numpy(), 1e-5)
+    err = check(y, zf, y_ref, zf_ref, wl.lengths.numpy(), wl.K.cpu().numpy(), 1e-5)
     print("bandpass16 rel-L2", float(err.max()))
 
 
