@@ -112,6 +112,8 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->hdr = reinterpret_cast<WsHeader*>(ws + L.hdr);
     p->chan = reinterpret_cast<ChanInfo*>(ws + L.chan);
     p->tb = reinterpret_cast<int64_t*>(ws + L.tb);
+    p->order = reinterpret_cast<int32_t*>(ws + L.order);
+    p->rp = reinterpret_cast<int64_t*>(ws + L.rp);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
     p->cdf = reinterpret_cast<CoefDF*>(ws + L.cdf);
     p->slots = reinterpret_cast<Slot*>(ws + L.slots);

@@ -34,169 +34,9 @@
 //  S8  the lane holding a channel's last sample writes zf.
 #include <cmath>
 
-#include "sos_common.cuh"
+#include "sos_kernels.cuh"
 
 namespace sosf {
-
-template <int N>
-struct Swz {
-    // 16-byte granule index within the tile -> physical granule.  A lane's
-    // chunk is N/4 granules; XOR with the chunk index (mod 8) makes both the
-    // row-wise (global <-> shared) and the chunk-wise (shared <-> registers)
-    // 128-bit accesses bank-conflict free.
-    static constexpr int kShift = (N == 16) ? 2 : (N == 32) ? 3 : 4;
-    __device__ __forceinline__ static int g(int G) { return G ^ ((G >> kShift) & 7); }
-    __device__ __forceinline__ static int e(int j) { return (g(j >> 2) << 2) | (j & 3); }
-};
-
-__device__ __forceinline__ dfm2 load_theta(const CoefDF* cd, int d) {
-    const float4 r0 = __ldg(&cd->theta_pow[d][0]);
-    const float4 r1 = __ldg(&cd->theta_pow[d][1]);
-    return dfm2{df{r0.x, r0.y}, df{r0.z, r0.w}, df{r1.x, r1.y}, df{r1.z, r1.w}};
-}
-
-// Reads one half (inc or agg) of a slot; true if all four words carry `tag`.
-__device__ __forceinline__ bool read_state(const unsigned long long* w, uint32_t tag, df& z1,
-                                           df& z2) {
-    unsigned long long w0, w1, w2, w3;
-    ld_relaxed_v2u64(w, w0, w1);
-    ld_relaxed_v2u64(w + 2, w2, w3);
-    z1 = df{word_value(w0), word_value(w1)};
-    z2 = df{word_value(w2), word_value(w3)};
-    return word_has(w0, tag) && word_has(w1, tag) && word_has(w2, tag) && word_has(w3, tag);
-}
-
-__device__ __forceinline__ void write_state(unsigned long long* w, uint32_t tag, df z1, df z2) {
-    st_relaxed_v2u64(w, tag_word(z1.hi, tag), tag_word(z1.lo, tag));
-    st_relaxed_v2u64(w + 2, tag_word(z2.hi, tag), tag_word(z2.lo, tag));
-}
-
-__device__ __forceinline__ df shfl_df(df v, int src) {
-    return df{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
-}
-
-__device__ __forceinline__ df shfl_xor_df(df v, int m) {
-    return df{__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m)};
-}
-
-// Incoming DF2T state of tile t (global index), section k, whose channel-local
-// index is ti >= 1.  Run by one full warp; every lane returns the same value.
-// Predecessor tiles publish their aggregate c (zero-state outgoing state) and,
-// once known, their inclusive value P (true outgoing state).  The state
-// entering tile t is Z_t = sum_{i<f} Theta^i c_{t-1-i} + Theta^f P_{t-1-f},
-// f the nearest predecessor with an inclusive value; lane i forms its term
-// with the precomputed Theta^i and the warp adds them up.  A window of 32
-// aggregates without an inclusive value is folded with Theta^32 and the walk
-// continues further back.  All of it in double-float.
-__device__ __noinline__ void lookback(const Params& p, int64_t t, int64_t ti, int k, uint32_t epoch,
-                         const CoefDF* cd, df& Z1, df& Z2) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t tag_inc = (epoch << 2) | kFlagInc, tag_agg = (epoch << 2) | kFlagAgg;
-    const Slot* sl = p.slots + (int64_t)k * p.cap_tiles;
-    // common case: the previous tile already published its inclusive value
-    {
-        df z1, z2;
-        const bool ok = read_state(sl[t - 1].inc, tag_inc, z1, z2);
-        if (__all_sync(0xffffffffu, ok)) {
-            Z1 = z1;
-            Z2 = z2;
-            return;
-        }
-    }
-    df acc1 = df{0.f, 0.f}, acc2 = df{0.f, 0.f};
-    dfm2 M = dfm_identity();
-    int64_t base = t - 1;
-    int64_t remaining = ti;
-    const dfm2 Ti = load_theta(cd, lane);
-    for (;;) {
-        const int cnt = (int)(remaining < 32 ? remaining : 32);
-        const int64_t j = base - lane;
-        const bool valid = lane < cnt;
-        uint32_t incm = 0;
-        int first = 32;
-        df v1 = df{0.f, 0.f}, v2 = df{0.f, 0.f};
-        uint32_t spins = 0;
-        for (;;) {
-            df i1, i2, a1, a2;
-            bool isinc = false, isagg = false;
-            if (valid) {
-                isinc = read_state(sl[j].inc, tag_inc, i1, i2);
-                isagg = read_state(sl[j].agg, tag_agg, a1, a2);
-            }
-            incm = __ballot_sync(0xffffffffu, isinc);
-            const uint32_t readym = __ballot_sync(0xffffffffu, isinc || isagg);
-            bool done = false;
-            if (incm) {
-                first = __ffs(incm) - 1;
-                const uint32_t need = first == 0 ? 0u : (0xffffffffu >> (32 - first));
-                done = (readym & need) == need;
-            } else if (cnt == 32 && readym == 0xffffffffu) {
-                first = 32;
-                done = true;
-            }
-            if (done) {
-                if (lane < first) {
-                    v1 = a1;
-                    v2 = a2;
-                } else if (lane == first) {
-                    v1 = i1;
-                    v2 = i2;
-                }
-                break;
-            }
-            ++spins;
-            if (spins > kSpinLimit) {
-                if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
-                Z1 = acc1;
-                Z2 = acc2;
-                return;
-            }
-            if ((spins & 63u) == 0u && ld_volatile_i32(&p.hdr->status) != 0) {
-                Z1 = acc1;
-                Z2 = acc2;
-                return;
-            }
-            __nanosleep(32);
-        }
-        // this window's sum: sum_i Theta^i v_i
-        df u1, u2;
-        if (first == 0) {
-            u1 = shfl_df(v1, 0);
-            u2 = shfl_df(v2, 0);
-        } else {
-            const bool use = lane <= first;  // first == 32: every lane
-            df t1 = df{0.f, 0.f}, t2 = df{0.f, 0.f};
-            if (use) dfm_affine(Ti, v1, v2, df{0.f, 0.f}, df{0.f, 0.f}, t1, t2);
-#pragma unroll
-            for (int m = 16; m >= 1; m >>= 1) {
-                t1 = df_add(t1, shfl_xor_df(t1, m));
-                t2 = df_add(t2, shfl_xor_df(t2, m));
-            }
-            u1 = t1;
-            u2 = t2;
-        }
-        // Z = acc + M u
-        df n1, n2;
-        dfm_affine(M, u1, u2, acc1, acc2, n1, n2);
-        acc1 = n1;
-        acc2 = n2;
-        if (incm) {
-            Z1 = acc1;
-            Z2 = acc2;
-            return;
-        }
-        // no inclusive value in this window: go 32 tiles further back
-        M = dfm_mul(M, load_theta(cd, 32));
-        base -= 32;
-        remaining -= 32;
-        if (remaining <= 0) {  // cannot happen: a channel's first tile is always inclusive
-            if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
-            Z1 = acc1;
-            Z2 = acc2;
-            return;
-        }
-    }
-}
 
 template <int N, int W>
 struct FwdKernel {
@@ -212,18 +52,21 @@ template <int W>
 struct SectionShared {
     float2 agg[W];  // zero-state state leaving each warp's group
     float2 win[W];  // true state entering each warp's group
+    LookbackShared<W + 1> lb;
 };
 
 // One section of the cascade on a data warp's register-resident chunk.
 template <int N, int W, bool FACT>
 __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int k, int c,
+                                             int64_t t, int64_t ti, uint32_t epoch,
+                                             const Coef32* cf, const CoefDF* cd,
                                              SectionShared<W>* sh, bool zf_owner, int mq,
                                              float* s_own) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const Coef32* cf = p.c32 + ((int64_t)c * p.kmax + k);
-    const float4 ab = __ldg(&cf->ab);
+    // data warp index (warp 0 of the CTA is the coordinator)
+    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 1;
+    const float4 ab = cf->ab;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
-    const float b0 = FACT ? 1.0f : __ldg(&cf->misc).x;
+    const float b0 = FACT ? 1.0f : cf->misc.x;
 
     // the section input at the channel's last sample (S8): the owning lane
     // parks its chunk in its own slice of the (idle) tile buffer so that the
@@ -263,7 +106,7 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
         const int d = 1 << j;
         const float t1 = __shfl_up_sync(0xffffffffu, S1, d);
         const float t2 = __shfl_up_sync(0xffffffffu, S2, d);
-        const float4 P = __ldg(&cf->phi_pow[j]);
+        const float4 P = cf->phi_pow[j];
         if (lane >= d) {
             S1 = fmaf(P.x, t1, fmaf(P.y, t2, S1));
             S2 = fmaf(P.z, t1, fmaf(P.w, t2, S2));
@@ -277,11 +120,15 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
     }
     if (lane == 31) sh->agg[warp] = make_float2(S1, S2);
     __syncthreads();  // B1: warp aggregates ready for the coordinator
+    if (ti > 0) {     // help the coordinator read the predecessors (S5)
+        df d1, d2;
+        lookback_cta<false, W + 1>(p, t, ti, k, epoch, cd, &sh->lb, 0, d1, d2);
+    }
     __syncthreads();  // B2: the coordinator has placed this warp's incoming state
     const float2 Zw = sh->win[warp];
 
     // fold the warp's true incoming state into this lane's
-    const float4 Pl = __ldg(&cf->lane_pow[lane]);
+    const float4 Pl = cf->lane_pow[lane];
     const float zin1 = fmaf(Pl.x, Zw.x, fmaf(Pl.y, Zw.y, E1));
     const float zin2 = fmaf(Pl.z, Zw.x, fmaf(Pl.w, Zw.y, E2));
 
@@ -304,21 +151,33 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
             f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
         }
         const float f2 = fmaf(b2, xq, -a2 * yq);
-        const float G = FACT ? __ldg(&cf->misc).y : 1.0f;
+        const float G = FACT ? cf->misc.y : 1.0f;
         p.zf[((int64_t)c * p.kmax + k) * 2 + 0] = f1 * G;
         p.zf[((int64_t)c * p.kmax + k) * 2 + 1] = f2 * G;
     }
 }
 
 // The coordinator warp's part of one section (S5): scan over the W warp
-// aggregates, publication of the tile's aggregate, look-back for the tile's
-// incoming state, publication of its outgoing state, and each warp's
-// incoming state.
+// aggregates, publication of the tile's aggregate, the look-back (with the
+// data warps' help) for the tile's incoming state, publication of its
+// outgoing state, and each warp's incoming state.
 template <int W>
 __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int64_t t, int64_t ti,
-                                              int64_t nt, uint32_t epoch, SectionShared<W>* sh) {
+                                              int64_t nt, uint32_t epoch, const Coef32* cf,
+                                              const CoefDF* cd, SectionShared<W>* sh) {
     const int lane = threadIdx.x & 31;
-    const Coef32* cf = p.c32 + ((int64_t)c * p.kmax + k);
+    // everything this section needs, read while the data warps compute
+    float4 Pr[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) Pr[r] = cf->psi_pow[r];
+    const float4 misc = cf->misc;
+    const float4 Pw = cf->psi_w[lane < 16 ? lane : 0];
+    const dfm2 Th = load_theta(cd, 1);
+    float zi1 = 0.f, zi2 = 0.f;
+    if (ti == 0 && p.zi) {
+        zi1 = p.zi[((int64_t)c * p.kmax + k) * 2 + 0];
+        zi2 = p.zi[((int64_t)c * p.kmax + k) * 2 + 1];
+    }
     __syncthreads();  // B1
     float A1 = 0.f, A2 = 0.f;
     if (lane < W) {
@@ -331,10 +190,9 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
         const int d = 1 << r;
         const float t1 = __shfl_up_sync(0xffffffffu, A1, d);
         const float t2 = __shfl_up_sync(0xffffffffu, A2, d);
-        const float4 P = __ldg(&cf->psi_pow[r]);
         if (lane >= d && lane < W) {
-            A1 = fmaf(P.x, t1, fmaf(P.y, t2, A1));
-            A2 = fmaf(P.z, t1, fmaf(P.w, t2, A2));
+            A1 = fmaf(Pr[r].x, t1, fmaf(Pr[r].y, t2, A1));
+            A2 = fmaf(Pr[r].z, t1, fmaf(Pr[r].w, t2, A2));
         }
     }
     float WE1 = __shfl_up_sync(0xffffffffu, A1, 1);
@@ -345,34 +203,26 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
     }
     const float C1 = __shfl_sync(0xffffffffu, A1, W - 1);
     const float C2 = __shfl_sync(0xffffffffu, A2, W - 1);
-    const CoefDF* cd = p.cdf + ((int64_t)c * p.kmax + k);
     const bool has_succ = ti + 1 < nt;
-    Slot* slot = p.slots + (int64_t)k * p.cap_tiles + t;
+    Slot& slot = p.slots[(int64_t)k * p.cap_tiles + t];
     df Z1, Z2;
     if (ti == 0) {
-        Z1 = df{0.f, 0.f};
-        Z2 = df{0.f, 0.f};
-        if (p.zi) {
-            const float gi = __ldg(&cf->misc).z;
-            const float* zi = p.zi + ((int64_t)c * p.kmax + k) * 2;
-            // zi / G_k, the exact product split into hi + lo
-            const float q1 = zi[0] * gi, q2 = zi[1] * gi;
-            Z1 = df{q1, fmaf(zi[0], gi, -q1)};
-            Z2 = df{q2, fmaf(zi[1], gi, -q2)};
-        }
+        // zi / G_k, the exact product split into hi + lo
+        const float gi = misc.z;
+        const float q1 = zi1 * gi, q2 = zi2 * gi;
+        Z1 = df{q1, fmaf(zi1, gi, -q1)};
+        Z2 = df{q2, fmaf(zi2, gi, -q2)};
     } else {
-        if (has_succ && lane == 0)
-            write_state(slot->agg, (epoch << 2) | kFlagAgg, df_from(C1), df_from(C2));
-        lookback(p, t, ti, k, epoch, cd, Z1, Z2);
+        if (has_succ && lane == 0) write_agg(slot, (epoch << 2) | kFlagAgg, C1, C2);
+        lookback_cta<false, W + 1>(p, t, ti, k, epoch, cd, &sh->lb, 0, Z1, Z2);
     }
     if (has_succ && lane == 0) {
         df P1, P2;
-        dfm_affine(load_theta(cd, 1), Z1, Z2, df_from(C1), df_from(C2), P1, P2);
-        write_state(slot->inc, (epoch << 2) | kFlagInc, P1, P2);
+        dfm_affine(Th, Z1, Z2, df_from(C1), df_from(C2), P1, P2);
+        write_inc(slot, (epoch << 2) | kFlagInc, P1, P2);
     }
     if (lane < W) {
         const float z1 = df_to_float(Z1), z2 = df_to_float(Z2);
-        const float4 Pw = __ldg(&cf->psi_w[lane]);
         sh->win[lane] = make_float2(fmaf(Pw.x, z1, fmaf(Pw.y, z2, WE1)),
                                     fmaf(Pw.z, z1, fmaf(Pw.w, z2, WE2)));
     }
@@ -387,11 +237,19 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     float* s_tile = reinterpret_cast<float*>(s_tile4);
     __shared__ SectionShared<W> sh;
     __shared__ int64_t s_t;
+    // the current channel's coefficient tables, staged once per channel
+    __shared__ Coef32 s_c32[kMaxSections];
+    __shared__ CoefDF s_cdf[kMaxSections];
+    int cur_c = -1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool coord = warp == W;
+    // Warp 0 coordinates, warps 1..W hold data.  The coordinator is the CTA's
+    // oldest warp: its short, latency-bound path is what every data warp
+    // waits for, and the warp schedulers favour older warps.
+    const bool coord = warp == 0;
     const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&p.hdr->epoch);
     const int64_t total = p.hdr->total_tiles;
+    const int64_t nrounds = p.hdr->nrounds;
 
     // final states that no tile writes: sections past K[c] are zero, an
     // empty channel keeps its initial state
@@ -412,23 +270,49 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     for (;;) {
         if (tid == 0) s_t = (int64_t)atomicAdd(&p.hdr->tile_counter, 1u);
         __syncthreads();
-        const int64_t t = s_t;
-        if (t >= total) break;
+        const int64_t d = s_t;  // dispatch index
+        if (d >= total) break;
 
-        // channel of tile t: the largest c with tb[c] <= t
-        int lo = 0, hi = p.C - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(&p.tb[mid]) <= t) lo = mid; else hi = mid - 1;
+        int c;
+        int64_t ti;
+        if (nrounds > 0) {
+            // interleaved: round r = the largest with rp[r] <= d, then the
+            // (d - rp[r])-th channel of the sorted order
+            int64_t lo = 0, hi = nrounds - 1;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (__ldg(&p.rp[mid]) <= d) lo = mid; else hi = mid - 1;
+            }
+            ti = lo;
+            c = __ldg(&p.order[d - __ldg(&p.rp[lo])]);
+        } else {
+            // channel by channel: the largest c with tb[c] <= d
+            int lo = 0, hi = p.C - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(&p.tb[mid]) <= d) lo = mid; else hi = mid - 1;
+            }
+            c = lo;
+            ti = d - __ldg(&p.tb[c]);
         }
-        const int c = lo;
         const ChanInfo ci = p.chan[c];
-        const int64_t ti = t - __ldg(&p.tb[c]);
+        const int64_t t = __ldg(&p.tb[c]) + ti;  // the tile's slot index (channel-major)
         const int64_t nt = ci.ntiles;
         const int64_t start = ti * KT::kTile;
         const int64_t rem = ci.len - start;
         const int r = (int)(rem < KT::kTile ? rem : KT::kTile);  // valid samples
         const float* src = p.x + ci.off + start;
+
+        if (c != cur_c) {  // CTA-uniform
+            constexpr int n32 = sizeof(Coef32) / sizeof(float4), ndf = sizeof(CoefDF) / sizeof(float4);
+            const float4* g32 = reinterpret_cast<const float4*>(p.c32 + (int64_t)c * p.kmax);
+            const float4* gdf = reinterpret_cast<const float4*>(p.cdf + (int64_t)c * p.kmax);
+            for (int i = tid; i < ci.K * n32; i += KT::kThreads)
+                reinterpret_cast<float4*>(s_c32)[i] = __ldg(g32 + i);
+            for (int i = tid; i < ci.K * ndf; i += KT::kThreads)
+                reinterpret_cast<float4*>(s_cdf)[i] = __ldg(gdf + i);
+            cur_c = c;
+        }
 
         // S2: global -> shared (swizzled), zero beyond the channel end; all
         // W + 1 warps take part
@@ -444,10 +328,11 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
         __syncthreads();
 
         if (coord) {
-            for (int k = 0; k < ci.K; ++k) coord_section<W>(p, k, c, t, ti, nt, epoch, &sh);
+            for (int k = 0; k < ci.K; ++k)
+                coord_section<W>(p, k, c, t, ti, nt, epoch, &s_c32[k], &s_cdf[k], &sh);
         } else {
             float v[N];
-            const int chunk = warp * 32 + lane;
+            const int chunk = (warp - 1) * 32 + lane;
 #pragma unroll
             for (int g = 0; g < N / 4; ++g) {
                 const float4 q = s_tile4[S::g(chunk * (N / 4) + g)];
@@ -466,13 +351,15 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             float* s_own = s_tile + chunk * N;
             if (ci.mode) {
                 for (int k = 0; k < ci.K; ++k)
-                    data_section<N, W, true>(p, v, k, c, &sh, zf_owner, mq, s_own);
-                const float G = __ldg(&p.c32[(int64_t)c * p.kmax + ci.K - 1].misc).y;
+                    data_section<N, W, true>(p, v, k, c, t, ti, epoch, &s_c32[k], &s_cdf[k], &sh,
+                                             zf_owner, mq, s_own);
+                const float G = s_c32[ci.K - 1].misc.y;
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] *= G;
             } else {
                 for (int k = 0; k < ci.K; ++k)
-                    data_section<N, W, false>(p, v, k, c, &sh, zf_owner, mq, s_own);
+                    data_section<N, W, false>(p, v, k, c, t, ti, epoch, &s_c32[k], &s_cdf[k], &sh,
+                                              zf_owner, mq, s_own);
             }
             // S7: registers -> shared (swizzled)
             __syncwarp();  // order the zf owner's scratch writes before the lanes' stores
@@ -526,8 +413,9 @@ struct KernelEntry {
      FwdKernel<N_, W_>::kSmem}
 
 static const KernelEntry kEntries[] = {
-    SOSF_ENTRY(16, 8, 3), SOSF_ENTRY(16, 16, 2), SOSF_ENTRY(32, 4, 4), SOSF_ENTRY(32, 8, 2),
-    SOSF_ENTRY(32, 16, 1), SOSF_ENTRY(64, 4, 2), SOSF_ENTRY(64, 8, 1),
+    SOSF_ENTRY(16, 8, 3),  SOSF_ENTRY(16, 16, 2), SOSF_ENTRY(32, 4, 4), SOSF_ENTRY(32, 7, 3),
+    SOSF_ENTRY(32, 8, 2),  SOSF_ENTRY(32, 16, 1), SOSF_ENTRY(64, 3, 4), SOSF_ENTRY(64, 4, 2),
+    SOSF_ENTRY(64, 8, 1),
 };
 
 bool forward_supported(int N, int W) {
@@ -553,11 +441,9 @@ cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t str
         if (err != cudaSuccess) return err;
     }
     if (s_occ[dev][idx] == 0) {
-        if (ke->smem > 48 * 1024) {
-            err = cudaFuncSetAttribute(ke->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)ke->smem);
-            if (err != cudaSuccess) return err;
-        }
+        err = cudaFuncSetAttribute(ke->fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)ke->smem);
+        if (err != cudaSuccess) return err;
         int occ = 0;
         err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ke->fn, (p.W + 1) * 32, ke->smem);
         if (err != cudaSuccess) return err;

@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     __shared__ double s_b0[kMaxSections];
     __shared__ int s_mode;
     __shared__ double s_G[kMaxSections];
-    // Phi^(2^j) j<5, Psi^(2^r) r<4, Theta^(2^i) i<6
-    __shared__ dfm2 s_chain[kMaxSections][15];
+    // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
+    __shared__ dfm2 s_chain[kMaxSections][20];
 
     if (tid == 0) p.chan[c].err = 0;
     __syncthreads();
@@ -178,33 +178,39 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     if (lane == 0) {
         const dfm2 A{df_of_double(-a1), df{1.f, 0.f}, df_of_double(-a2), df{0.f, 0.f}};
         dfm2 P = A;
-        for (int n = 1; n < N; n <<= 1) P = dfm_mul(P, P);  // A^N
+        for (int n = 1; n < N; n <<= 1) P = dfm_mul(P, P);  // A^N (N a power of two)
         s_chain[k][0] = P;
         for (int j = 1; j < 5; ++j) s_chain[k][j] = dfm_mul(s_chain[k][j - 1], s_chain[k][j - 1]);
         s_chain[k][5] = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
-        for (int r = 1; r < 4; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
-        dfm2 Th = s_chain[k][5];
-        for (int w = 1; w < W; w <<= 1) Th = dfm_mul(Th, Th);  // Theta = Psi^W
-        s_chain[k][9] = Th;
-        for (int i = 1; i < 6; ++i) s_chain[k][9 + i] = dfm_mul(s_chain[k][8 + i], s_chain[k][8 + i]);
+        for (int r = 1; r < 5; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
+        dfm2 Th = dfm_identity();  // Theta = Psi^W, any W <= 31
+        for (int r = 0; r < 5; ++r)
+            if ((W >> r) & 1) Th = dfm_mul(Th, s_chain[k][5 + r]);
+        s_chain[k][10] = Th;
+        for (int i = 1; i < 10; ++i) s_chain[k][10 + i] = dfm_mul(s_chain[k][9 + i], s_chain[k][9 + i]);
     }
     __syncwarp();
 
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
     CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
     {
-        // Phi^lane and Theta^lane by binary powering, each lane its own entry
-        dfm2 P = dfm_identity(), Q = dfm_identity();
+        // Phi^lane, Theta^lane and Theta^(32 lane) by binary powering
+        dfm2 P = dfm_identity(), Q = dfm_identity(), R = dfm_identity();
         for (int j = 0; j < 5; ++j)
             if ((lane >> j) & 1) {
                 P = dfm_mul(P, s_chain[k][j]);
-                Q = dfm_mul(Q, s_chain[k][9 + j]);
+                Q = dfm_mul(Q, s_chain[k][10 + j]);
+                R = dfm_mul(R, s_chain[k][15 + j]);
             }
         out32->lane_pow[lane] = to_f4(P);
         outdf->theta_pow[lane][0] = make_float4(Q.a.hi, Q.a.lo, Q.b.hi, Q.b.lo);
         outdf->theta_pow[lane][1] = make_float4(Q.c.hi, Q.c.lo, Q.d.hi, Q.d.lo);
+        if (lane < 18) {
+            outdf->theta_hi[lane][0] = make_float4(R.a.hi, R.a.lo, R.b.hi, R.b.lo);
+            outdf->theta_hi[lane][1] = make_float4(R.c.hi, R.c.lo, R.d.hi, R.d.lo);
+        }
         if (lane == 0) {
-            const dfm2 T32 = s_chain[k][14];
+            const dfm2 T32 = s_chain[k][15];
             outdf->theta_pow[32][0] = make_float4(T32.a.hi, T32.a.lo, T32.b.hi, T32.b.lo);
             outdf->theta_pow[32][1] = make_float4(T32.c.hi, T32.c.lo, T32.d.hi, T32.d.lo);
         }
@@ -225,11 +231,103 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     }
 }
 
+// Interleaved dispatch order (one CTA of 1024 threads, runs after
+// plan_kernel).  Tiles are handed out round by round: round r holds tile r of
+// every channel that has more than r tiles.  Then a tile's predecessor in its
+// own channel was dispatched a whole round earlier and has usually finished,
+// so the look-back finds its outgoing state at once.  Channels are sorted by
+// decreasing tile count (bitonic sort in shared memory), which makes each
+// round a prefix of that order.  With more than kMaxSortChannels channels the
+// kernel leaves nrounds = 0 and tiles go channel by channel.
+__global__ void __launch_bounds__(1024) order_kernel(Params p) {
+    extern __shared__ unsigned long long s_key[];
+    const int tid = threadIdx.x, C = p.C;
+    if (C > kMaxSortChannels) {
+        if (tid == 0) p.hdr->nrounds = 0;
+        return;
+    }
+    int n = 1;
+    while (n < C) n <<= 1;
+    for (int i = tid; i < n; i += blockDim.x) {
+        // ascending sort of (MAX - ntiles, channel): decreasing tile count,
+        // then increasing channel index; padding sorts last
+        const unsigned long long nt = i < C ? (unsigned long long)p.chan[i].ntiles : 0ull;
+        s_key[i] = i < C ? (((0xffffffffull - nt) << 32) | (unsigned)i) : ~0ull;
+    }
+    __syncthreads();
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < n; i += blockDim.x) {
+                const int j = i ^ stride;
+                if (j > i) {
+                    const bool up = (i & size) == 0;
+                    const unsigned long long a = s_key[i], b = s_key[j];
+                    if ((a > b) == up) {
+                        s_key[i] = b;
+                        s_key[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < C; i += blockDim.x) p.order[i] = (int32_t)(s_key[i] & 0xffffffffu);
+    const int64_t nrounds = C > 0 ? (int64_t)(0xffffffffull - (s_key[0] >> 32)) : 0;
+    // rp[r] = sum over rounds q < r of (channels with more than q tiles)
+    __shared__ int64_t s_carry;
+    __shared__ int64_t s_wsum[32];
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int64_t base = 0; base <= nrounds; base += blockDim.x) {
+        const int64_t r = base + tid;
+        int64_t cnt = 0;
+        if (r < nrounds) {
+            // channels with ntiles > r: a prefix of the sorted order (binary search)
+            int lo = 0, hi = C;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int64_t nt = (int64_t)(0xffffffffull - (s_key[mid] >> 32));
+                if (nt > r) lo = mid + 1; else hi = mid;
+            }
+            cnt = lo;
+        }
+        int64_t inc = cnt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        int64_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        const int64_t carry = s_carry;
+        if (r <= nrounds) p.rp[r] = carry + wpre + inc - cnt;
+        __syncthreads();
+        if (tid == blockDim.x - 1) s_carry = carry + wpre + inc;
+        __syncthreads();
+    }
+    if (tid == 0) p.hdr->nrounds = nrounds;
+}
+
 }  // namespace sosf
 
 namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream) {
     plan_kernel<<<p.C + 1, 256, 0, stream>>>(p);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    int n = 1;
+    while (n < p.C && n < kMaxSortChannels) n <<= 1;
+    const size_t smem = p.C <= kMaxSortChannels ? sizeof(unsigned long long) * (size_t)n : 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        err = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(unsigned long long) * kMaxSortChannels));
+        if (err != cudaSuccess) return err;
+        attr_set = true;
+    }
+    order_kernel<<<1, 1024, smem, stream>>>(p);
     return cudaGetLastError();
 }
 }  // namespace sosf

@@ -24,6 +24,7 @@ constexpr int kMaxSections = SOS_MAX_SECTIONS;
 constexpr uint32_t kFlagAgg = 1;   // tile aggregate of one section published
 constexpr uint32_t kFlagInc = 2;   // tile inclusive state (outgoing state) published
 constexpr uint32_t kSpinLimit = 1u << 21;
+constexpr int kMaxSortChannels = 8192;  // interleaved dispatch up to this many channels
 
 // ---------------------------------------------------------------------------
 // workspace
@@ -37,7 +38,8 @@ struct WsHeader {
     int64_t total_tiles;    // tiles of the latest call (device view)
     int32_t nchan;          // channels of the latest call
     uint32_t done;          // CTAs of the running filter launch that have finished
-    int64_t pad1[4];
+    int64_t nrounds;        // interleaved dispatch: rounds (longest channel's tiles); 0 = channel-major
+    int64_t pad1[3];
 };
 static_assert(sizeof(WsHeader) == 64, "header size");
 
@@ -65,24 +67,28 @@ struct __align__(16) Coef32 {
 };
 
 // Per (channel, section) double-float powers of the tile transition
-// Theta = A^T (T = tile length) for the cross-tile composition: entry d holds
-// Theta^d, d = 0..32, as (a.hi, a.lo, b.hi, b.lo), (c.hi, c.lo, d.hi, d.lo).
+// Theta = A^T (T = tile length) for the cross-tile composition, each as
+// (a.hi, a.lo, b.hi, b.lo), (c.hi, c.lo, d.hi, d.lo):
+// theta_pow[d] = Theta^d, d = 0..32; theta_hi[j] = Theta^(32 j), j = 0..17.
 struct __align__(16) CoefDF {
     float4 theta_pow[33][2];
+    float4 theta_hi[18][2];
 };
 
 // One look-back slot per (section, tile): the tile's inclusive (true
-// outgoing) state and its aggregate (zero-state outgoing) state, each as four
-// 64-bit words (z1.hi, z1.lo, z2.hi, z2.lo).  Every word carries its own tag
-// (epoch << 2 | kind) in the low 32 bits, so a reader validates what it read
-// word by word: one L2 round trip, no separate flag, no fence.
+// outgoing) state as four 64-bit words (z1.hi, z1.lo, z2.hi, z2.lo) and its
+// aggregate (zero-state outgoing) state as two (z1, z2; the aggregate is an
+// FP32 quantity).  Every word carries its own tag (epoch << 2 | kind) in the
+// low 32 bits, so a reader validates what it read word by word: one L2 round
+// trip, no separate flag, no fence.
 struct __align__(64) Slot {
     unsigned long long inc[4];
-    unsigned long long agg[4];
+    unsigned long long agg[2];
+    unsigned long long pad[2];
 };
 
 struct WsLayout {
-    size_t hdr, chan, tb, c32, cdf, slots, total;
+    size_t hdr, chan, tb, order, rp, c32, cdf, slots, total;
     int64_t cap_tiles;
 };
 
@@ -94,6 +100,8 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.hdr = o;   o = align_up(o + sizeof(WsHeader), 256);
     L.chan = o;  o = align_up(o + sizeof(ChanInfo) * (size_t)C, 256);
     L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
+    L.order = o; o = align_up(o + sizeof(int32_t) * (size_t)C, 256);
+    L.rp = o;    o = align_up(o + sizeof(int64_t) * ((size_t)(cap_tiles > 0 ? cap_tiles : 0) + 2), 256);
     L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
     L.cdf = o;   o = align_up(o + sizeof(CoefDF) * (size_t)C * kmax, 256);
     const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);
@@ -115,6 +123,8 @@ struct Params {
     WsHeader* hdr;
     ChanInfo* chan;
     int64_t* tb;         // tile prefix [C + 1]
+    int32_t* order;      // channels by decreasing tile count (interleaved dispatch)
+    int64_t* rp;         // tiles dispatched before round r [nrounds + 1]
     Coef32* c32;
     CoefDF* cdf;
     Slot* slots;         // [kmax][cap_tiles]

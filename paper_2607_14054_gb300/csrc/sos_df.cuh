@@ -42,6 +42,15 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return df_fast_two_sum(s.hi, s.lo);
 }
 
+// Cheaper addition (one TwoSum instead of two): the low parts are added
+// without compensation, so the result carries about 2^-44 relative error
+// unless the operands nearly cancel.  Used where terms of similar magnitude
+// are summed (look-back compositions).
+__device__ __forceinline__ df df_add_fast(df a, df b) {
+    const df s = df_two_sum(a.hi, b.hi);
+    return df_fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
+}
+
 __device__ __forceinline__ df df_mul(df a, df b) {
     const float p = a.hi * b.hi;
     float e = fmaf(a.hi, b.hi, -p);
@@ -71,6 +80,13 @@ __device__ __forceinline__ void dfm_affine(const dfm2& M, df u1, df u2, df c1, d
                                            df& y2) {
     y1 = df_add(df_add(df_mul(M.a, u1), df_mul(M.b, u2)), c1);
     y2 = df_add(df_add(df_mul(M.c, u1), df_mul(M.d, u2)), c2);
+}
+
+// y = M u + c with the cheaper additions
+__device__ __forceinline__ void dfm_affine_fast(const dfm2& M, df u1, df u2, df c1, df c2, df& y1,
+                                                df& y2) {
+    y1 = df_add_fast(df_add_fast(df_mul(M.a, u1), df_mul(M.b, u2)), c1);
+    y2 = df_add_fast(df_add_fast(df_mul(M.c, u1), df_mul(M.d, u2)), c2);
 }
 
 __device__ __forceinline__ float df_to_float(df a) { return a.hi + a.lo; }

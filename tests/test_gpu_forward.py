@@ -15,7 +15,7 @@ from synth import rng, workloads
 
 pytestmark = pytest.mark.gpu
 
-TUNINGS = [(32, 8), (16, 8), (64, 4), (32, 4), (32, 16), (16, 16), (64, 8)]
+TUNINGS = [(32, 8), (16, 8), (64, 4), (32, 4), (32, 16), (16, 16), (64, 8), (32, 7), (64, 3)]
 
 
 def _lib():
