@@ -116,7 +116,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->rp = reinterpret_cast<int64_t*>(ws + L.rp);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
     p->cdf = reinterpret_cast<CoefDF*>(ws + L.cdf);
-    p->slots = reinterpret_cast<Slot*>(ws + L.slots);
+    p->words = reinterpret_cast<unsigned long long*>(ws + L.slots);
     p->cap_tiles = tiles;
     p->C = n_channels;
     p->kmax = kmax;

@@ -52,7 +52,6 @@ template <int W>
 struct SectionShared {
     float2 agg[W];  // zero-state state leaving each warp's group
     float2 win[W];  // true state entering each warp's group
-    LookbackShared<W + 1> lb;
 };
 
 // One section of the cascade on a data warp's register-resident chunk.
@@ -120,10 +119,6 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
     }
     if (lane == 31) sh->agg[warp] = make_float2(S1, S2);
     __syncthreads();  // B1: warp aggregates ready for the coordinator
-    if (ti > 0) {     // help the coordinator read the predecessors (S5)
-        df d1, d2;
-        lookback_cta<false, W + 1>(p, t, ti, k, epoch, cd, &sh->lb, 0, d1, d2);
-    }
     __syncthreads();  // B2: the coordinator has placed this warp's incoming state
     const float2 Zw = sh->win[warp];
 
@@ -204,7 +199,7 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
     const float C1 = __shfl_sync(0xffffffffu, A1, W - 1);
     const float C2 = __shfl_sync(0xffffffffu, A2, W - 1);
     const bool has_succ = ti + 1 < nt;
-    Slot& slot = p.slots[(int64_t)k * p.cap_tiles + t];
+    const Words Wd = section_words(p, k);
     df Z1, Z2;
     if (ti == 0) {
         // zi / G_k, the exact product split into hi + lo
@@ -213,13 +208,13 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
         Z1 = df{q1, fmaf(zi1, gi, -q1)};
         Z2 = df{q2, fmaf(zi2, gi, -q2)};
     } else {
-        if (has_succ && lane == 0) write_agg(slot, (epoch << 2) | kFlagAgg, C1, C2);
-        lookback_cta<false, W + 1>(p, t, ti, k, epoch, cd, &sh->lb, 0, Z1, Z2);
+        if (has_succ && lane == 0) write_agg(Wd, t, (epoch << 2) | kFlagAgg, C1, C2);
+        lookback_warp<false>(p, t, ti, k, epoch, cd, Z1, Z2);
     }
     if (has_succ && lane == 0) {
         df P1, P2;
         dfm_affine(Th, Z1, Z2, df_from(C1), df_from(C2), P1, P2);
-        write_inc(slot, (epoch << 2) | kFlagInc, P1, P2);
+        write_inc(Wd, t, (epoch << 2) | kFlagInc, P1, P2);
     }
     if (lane < W) {
         const float z1 = df_to_float(Z1), z2 = df_to_float(Z2);

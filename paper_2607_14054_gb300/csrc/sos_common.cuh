@@ -75,17 +75,15 @@ struct __align__(16) CoefDF {
     float4 theta_hi[18][2];
 };
 
-// One look-back slot per (section, tile): the tile's inclusive (true
-// outgoing) state as four 64-bit words (z1.hi, z1.lo, z2.hi, z2.lo) and its
-// aggregate (zero-state outgoing) state as two (z1, z2; the aggregate is an
-// FP32 quantity).  Every word carries its own tag (epoch << 2 | kind) in the
-// low 32 bits, so a reader validates what it read word by word: one L2 round
-// trip, no separate flag, no fence.
-struct __align__(64) Slot {
-    unsigned long long inc[4];
-    unsigned long long agg[2];
-    unsigned long long pad[2];
-};
+// Look-back words, per (section, tile): the tile's inclusive (true outgoing)
+// state as four 64-bit words (z1.hi, z1.lo, z2.hi, z2.lo) and its aggregate
+// (zero-state outgoing) state as two (z1, z2; the aggregate is an FP32
+// quantity).  Every word carries its own tag (epoch << 2 | kind) in the low
+// 32 bits, so a reader validates what it read word by word: one L2 round
+// trip, no separate flag, no fence.  Stored as structure of arrays, word w of
+// tile t in section k at ((k * kWords + w) * cap_tiles + t), so that 32 lanes
+// reading 32 consecutive tiles make one coalesced access.
+constexpr int kWords = 6;  // inc z1.hi, z1.lo, z2.hi, z2.lo, agg z1, z2
 
 struct WsLayout {
     size_t hdr, chan, tb, order, rp, c32, cdf, slots, total;
@@ -105,7 +103,7 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
     L.cdf = o;   o = align_up(o + sizeof(CoefDF) * (size_t)C * kmax, 256);
     const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);
-    L.slots = o; o = align_up(o + sizeof(Slot) * nt * kmax, 256);
+    L.slots = o; o = align_up(o + sizeof(unsigned long long) * kWords * nt * kmax, 256);
     L.total = o;
     L.cap_tiles = cap_tiles;
     return L;
@@ -127,7 +125,7 @@ struct Params {
     int64_t* rp;         // tiles dispatched before round r [nrounds + 1]
     Coef32* c32;
     CoefDF* cdf;
-    Slot* slots;         // [kmax][cap_tiles]
+    unsigned long long* words;  // look-back words [kmax][kWords][cap_tiles]
     int64_t cap_tiles;
     int32_t C;
     int32_t kmax;
