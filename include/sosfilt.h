@@ -136,6 +136,32 @@ sos_status sos_apply(const float *x, int32_t n_channels, int32_t kmax,
                      const int64_t *lengths_host, const float *zi, float *y, float *zf,
                      void *workspace, size_t ws_bytes, const sos_tuning *tuning, void *stream);
 
+/* sos_filter without a caller-allocated workspace (the paper has no
+ * counterpart; this is a deployment convenience).  Some callers cannot call
+ * cudaMalloc at all: real-time audio or control callbacks where its latency
+ * and implicit device synchronisation are not allowed, plug-ins running
+ * inside a host application that owns the device allocator, and services
+ * that must not grow their memory footprint after start-up.  This entry point
+ * allocates nothing: its scratch is a fixed 8 MiB array in the library's own
+ * device memory (held by every GPU that loads the library until the process
+ * exits).  The caller still provides x, sos, K, lengths, zi, y and zf exactly
+ * as for sos_filter.
+ *   - The first call on a device looks up the array's device address and
+ *     zeroes it (a synchronous cudaMemset); make that first call before any
+ *     stream capture.  It allocates nothing and calls no allocating routine.
+ *   - Sizes whose workspace (sos_workspace_size) exceeds 8 MiB are rejected
+ *     with SOS_ERR_WORKSPACE; nothing is enqueued.
+ *   - Every call shares the one array and leaves its contents behind; calls
+ *     that overlap on the GPU (different streams without ordering, or other
+ *     host threads) race with each other and give wrong results.
+ *   - device_status: NULL, or a host int32 that receives the device-side
+ *     status of this call; passing it makes the call wait for `stream`.
+ * Returns SOS_OK once the work is enqueued (and, with device_status, done). */
+sos_status sos_filter_static(const float *x, const double *sos, const int32_t *K,
+                             int32_t n_channels, int32_t kmax, const int64_t *lengths,
+                             const int64_t *lengths_host, const float *zi, float *y, float *zf,
+                             const sos_tuning *tuning, void *stream, int32_t *device_status);
+
 /* Waits for `stream`, then returns (and clears) the device-side status word
  * of the most recent call that used this workspace. */
 sos_status sos_device_status(void *workspace, void *stream);

@@ -72,6 +72,9 @@ def load(build_if_missing: bool = False):
         lib.sos_prepare.restype = ctypes.c_int
         lib.sos_apply.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
         lib.sos_apply.restype = ctypes.c_int
+        lib.sos_filter_static.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, tp, vp,
+                                          ctypes.POINTER(ctypes.c_int32)]
+        lib.sos_filter_static.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
         _lib = lib
@@ -116,6 +119,18 @@ def sos_apply(x, n_channels, kmax, lengths_host, zi, y, zf, ws, ws_bytes, tuning
     V = ctypes.c_void_p
     return int(load().sos_apply(V(x), n_channels, kmax, V(lengths_host), V(zi or None), V(y),
                                 V(zf or None), V(ws), ws_bytes, _tuning(tuning), V(stream)))
+
+
+def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y, zf, tuning,
+                      stream, want_status: bool = True):
+    """Returns (status, device_status or None)."""
+    V = ctypes.c_void_p
+    ds = ctypes.c_int32(0)
+    st = int(load().sos_filter_static(V(x), V(sos), V(K), n_channels, kmax, V(lengths),
+                                      V(lengths_host), V(zi or None), V(y), V(zf or None),
+                                      _tuning(tuning), V(stream),
+                                      ctypes.byref(ds) if want_status else None))
+    return st, (int(ds.value) if want_status else None)
 
 
 def sos_device_status(ws_ptr: int, stream: int) -> int:

@@ -1,7 +1,6 @@
 // C ABI of the library (declared in include/sosfilt.h): argument checks,
 // workspace carving and the two launches of one call (plan, forward).
 #include <cstring>
-#include <vector>
 
 #include "sos_common.cuh"
 
@@ -208,17 +207,21 @@ sos_status sos_device_status(void* workspace, void* stream) {
         return SOS_ERR_CUDA;
     int32_t result = h.status;
     if (result == 0 && h.nchan > 0) {
-        // channel table sits right after the header (see ws_layout)
+        // channel table sits right after the header (see ws_layout); read it in
+        // fixed-size pieces (no host allocation)
         const WsLayout L = ws_layout(h.nchan, 1, 1);
-        std::vector<ChanInfo> ch((size_t)h.nchan);
-        if (cudaMemcpy(ch.data(), static_cast<char*>(workspace) + L.chan,
-                       sizeof(ChanInfo) * ch.size(), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return SOS_ERR_CUDA;
-        for (const auto& ci : ch)
-            if (ci.err) {
-                result = ci.err;
-                break;
-            }
+        ChanInfo buf[128];
+        for (int32_t c0 = 0; c0 < h.nchan && result == 0; c0 += 128) {
+            const int32_t n = h.nchan - c0 < 128 ? h.nchan - c0 : 128;
+            if (cudaMemcpy(buf, static_cast<char*>(workspace) + L.chan + sizeof(ChanInfo) * c0,
+                           sizeof(ChanInfo) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return SOS_ERR_CUDA;
+            for (int32_t i = 0; i < n; ++i)
+                if (buf[i].err) {
+                    result = buf[i].err;
+                    break;
+                }
+        }
     }
     const int32_t zero = 0;
     if (cudaMemcpy(&static_cast<WsHeader*>(workspace)->status, &zero, sizeof(zero),
