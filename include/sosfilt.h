@@ -71,7 +71,20 @@ typedef enum sos_status {
  *             (0 = default 8).
  *   algo:     recursive-stage solver: 0 = default, 1 = PH (Sec. VI-B).
  *   flags:    bit 0 (SOS_FLAG_CHECK_STABLE): reject sections whose poles are
- *             not strictly inside the unit circle. */
+ *             not strictly inside the unit circle.
+ *             bit 1 (SOS_FLAG_CARRY_ONLY): carry every channel's state between
+ *             tiles by the decoupled look-back, even where the channel's
+ *             memory horizon would let its tiles overlap and start from zero
+ *             state (same results to rounding; for testing and tuning).
+ *
+ * Cross-tile state.  The plan bounds each channel's impulse-response tail by
+ * partial fractions over its poles and finds its memory horizon P: the warm-up
+ * after which the state a tile would drop changes the output by less than
+ * 2^-30 relative.  If P <= T/2, the channel's tiles overlap by P samples and
+ * each starts from zero state (no cross-tile dependency); otherwise (poles
+ * near or on the unit circle, coincident poles) the DF2T state of every
+ * section is carried by a decoupled look-back composing FP64-accurate affine
+ * maps (Sec. V's group hand-off made parallel). */
 typedef struct sos_tuning {
     int32_t n_blocks;
     int32_t warps;
@@ -80,6 +93,7 @@ typedef struct sos_tuning {
 } sos_tuning;
 
 #define SOS_FLAG_CHECK_STABLE 1
+#define SOS_FLAG_CARRY_ONLY 2
 #define SOS_MAX_SECTIONS 8
 
 /* Bytes of device workspace needed for a call with these sizes.
@@ -165,6 +179,17 @@ sos_status sos_filter_static(const float *x, const double *sos, const int32_t *K
 /* Waits for `stream`, then returns (and clears) the device-side status word
  * of the most recent call that used this workspace. */
 sos_status sos_device_status(void *workspace, void *stream);
+
+/* Waits for `stream`, then copies from the channel table of the most recent
+ * sos_prepare on this workspace, for channels [first, first + count): the
+ * memory horizon P of each (>= 0: tiles overlap by P samples and start from
+ * zero state; -1: the state is carried by the look-back) into horizon[i] and
+ * its tile count into tiles[i] (host arrays of `count` entries; either may be
+ * NULL).  Reads the table in fixed pieces: no allocation.  SOS_ERR_ARG if the
+ * range is outside the channels of that call.  This query has no counterpart
+ * in the paper; it reports how the plan split the work. */
+sos_status sos_plan_query(void *workspace, int32_t first, int32_t count, int32_t *horizon,
+                          int32_t *tiles, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *sos_status_str(sos_status status);

@@ -126,6 +126,19 @@ class SosFilter:
             raise SosError(st, "sos_apply")
         return y, zf
 
+    def plan_info(self):
+        """(horizon, tiles) per channel from the latest prepare: int32 host
+        tensors; horizon -1 marks channels whose state is carried by the
+        look-back."""
+        h = torch.empty(self.n_channels, dtype=torch.int32)
+        t = torch.empty(self.n_channels, dtype=torch.int32)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = _abi.sos_plan_query(self.workspace.data_ptr(), 0, self.n_channels, h.data_ptr(),
+                                 t.data_ptr(), stream)
+        if st != 0:
+            raise SosError(st, "sos_plan_query")
+        return h, t
+
     def device_status(self) -> int:
         """Synchronises the current stream and returns the device-side status
         of the latest call (0 = OK)."""

@@ -18,6 +18,7 @@ _lib = None
 
 SOS_OK = 0
 SOS_FLAG_CHECK_STABLE = 1
+SOS_FLAG_CARRY_ONLY = 2
 SOS_MAX_SECTIONS = 8
 
 STATUS_NAMES = {
@@ -77,6 +78,8 @@ def load(build_if_missing: bool = False):
         lib.sos_filter_static.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
+        lib.sos_plan_query.argtypes = [vp, i32, i32, vp, vp, vp]
+        lib.sos_plan_query.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -135,6 +138,14 @@ def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y,
 
 def sos_device_status(ws_ptr: int, stream: int) -> int:
     return int(load().sos_device_status(ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream)))
+
+
+def sos_plan_query(ws_ptr: int, first: int, count: int, horizon_ptr: int, tiles_ptr: int,
+                   stream: int) -> int:
+    """Host pointers are integers (0 for NULL)."""
+    V = ctypes.c_void_p
+    return int(load().sos_plan_query(V(ws_ptr), first, count, V(horizon_ptr or None),
+                                     V(tiles_ptr or None), V(stream)))
 
 
 def sos_status_str(status: int) -> str:

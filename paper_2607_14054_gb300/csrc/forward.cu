@@ -29,7 +29,10 @@
 //            (2 FMAs per sample, like Eq. PH_forward, without a table).
 //  S5  cross-warp (shared memory, scan with Psi^(2^r)) and cross-tile
 //      (decoupled look-back over FP64 affine maps z -> Theta z + c, the GPU
-//      form of the inter-group hand-off of Sec. V) carry of the state;
+//      form of the inter-group hand-off of Sec. V) carry of the state.  A
+//      channel whose impulse response dies out within half a tile (its
+//      memory horizon P, computed by the plan) needs no carry: its tiles
+//      overlap by P samples and start from zero state;
 //  S7  de-permutation through shared memory and coalesced stores;
 //  S8  the lane holding a channel's last sample writes zf.
 #include <cmath>
@@ -54,18 +57,89 @@ struct SectionShared {
     float2 win[W];  // true state entering each warp's group
 };
 
+// Hand-off between consecutive data warps (tiles within a channel's memory
+// horizon): the true state leaving warp w's group in section k, passed to
+// warp w + 1 through shared memory and an mbarrier of arrival count 1.  The
+// producer's arrive releases the value, the consumer's try_wait acquires it;
+// a waiting warp is suspended by the hardware instead of polling, so it takes
+// no issue slots from the warps it waits for.  Each barrier completes one
+// phase per use; every data warp keeps the parity of section k's barriers in
+// bit k of its own phase mask (all warps of a tile process the same sections).
+template <int W>
+struct HandOff {
+    float2 val[kMaxSections][W];
+    unsigned long long bar[kMaxSections][W];
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* a) {
+    return (unsigned)__cvta_generic_to_shared(a);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_u32(b))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Store of the hand-off value and arrive, both predicated on `pred` inside
+// the asm block (no branch, so the warp stays converged).
+__device__ __forceinline__ void mbar_publish(float2* v, float a, float b, unsigned long long* bar,
+                                             bool pred) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b64 st;\n\tsetp.ne.u32 p, %4, 0;\n\t"
+        "@p st.shared.v2.f32 [%0], {%1, %2};\n\t"
+        "@p mbarrier.arrive.shared::cta.b64 st, [%3];\n\t}" ::"r"(smem_u32(v)),
+        "f"(a), "f"(b), "r"(smem_u32(bar)), "r"((unsigned)pred)
+        : "memory");
+}
+
+// bound on try_wait calls in one hand-off (each call may suspend the warp
+// for a while before returning false)
+constexpr uint32_t kHandOffLimit = 1u << 20;
+
 // One section of the cascade on a data warp's register-resident chunk.
-template <int N, int W, bool FACT>
+// CHAIN = false: the warp's incoming state comes from the coordinator warp
+// (CTA barriers B1/B2, cross-tile look-back).  CHAIN = true (tile within the
+// channel's memory horizon, no cross-tile carry): warp 0 starts from the
+// tile's own initial state and every other warp waits only for its
+// predecessor's hand-off, z_out(w) = Psi z_in(w) + agg(w).
+template <int N, int W, bool FACT, bool CHAIN>
 __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int k, int c,
                                              int64_t t, int64_t ti, uint32_t epoch,
                                              const Coef32* cf, const CoefDF* cd,
                                              SectionShared<W>* sh, bool zf_owner, int mq,
-                                             float* s_own) {
-    // data warp index (warp 0 of the CTA is the coordinator)
-    const int lane = threadIdx.x & 31, warp = (threadIdx.x >> 5) - 1;
+                                             float* s_own, HandOff<W>* ho, uint32_t& ph) {
+    // position of this data warp's group in the tile (warp 0 of the CTA is
+    // the coordinator; CTA warp j holds group W - j, so that the groups the
+    // in-tile carry reaches last belong to the oldest warps, which the warp
+    // schedulers favour)
+    const int lane = threadIdx.x & 31, warp = W - (int)(threadIdx.x >> 5);
     const float4 ab = cf->ab;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
     const float b0 = FACT ? 1.0f : cf->misc.x;
+    // (CHAIN) the tile's initial state, needed by warp 0 only: zi / G_k on a
+    // channel's first tile, zero state on the others
+    float zt1 = 0.f, zt2 = 0.f;
+    if (CHAIN && warp == 0 && ti == 0 && p.zi) {
+        const float gi = cf->misc.z;
+        zt1 = p.zi[((int64_t)c * p.kmax + k) * 2 + 0] * gi;
+        zt2 = p.zi[((int64_t)c * p.kmax + k) * 2 + 1] * gi;
+    }
 
     // the section input at the channel's last sample (S8): the owning lane
     // parks its chunk in its own slice of the (idle) tile buffer so that the
@@ -117,10 +191,43 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
         E1 = 0.f;
         E2 = 0.f;
     }
-    if (lane == 31) sh->agg[warp] = make_float2(S1, S2);
-    __syncthreads();  // B1: warp aggregates ready for the coordinator
-    __syncthreads();  // B2: the coordinator has placed this warp's incoming state
-    const float2 Zw = sh->win[warp];
+    float2 Zw;
+    if (!CHAIN) {
+        if (lane == 31) sh->agg[warp] = make_float2(S1, S2);
+        __syncthreads();  // B1: warp aggregates ready for the coordinator
+        __syncthreads();  // B2: the coordinator has placed this warp's incoming state
+        Zw = sh->win[warp];
+    } else {
+        // The whole warp waits and the publication is predicated inside one
+        // asm block: a branch taken by one lane would leave the warp diverged
+        // into the shuffles that follow, which then run several times slower.
+        float q1 = zt1, q2 = zt2;
+        const unsigned par = (ph >> k) & 1u;
+        ph ^= 1u << k;
+        if (warp > 0) {
+            // bounded wait for the predecessor warp's hand-off
+            unsigned long long* b = &ho->bar[k][warp - 1];
+            for (uint32_t it = 0;; ++it) {
+                const bool ok = mbar_try_wait(b, par);
+                if (__all_sync(0xffffffffu, ok)) break;
+                if (it >= kHandOffLimit) {
+                    if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            const float2 z = ho->val[k][warp - 1];
+            q1 = z.x;
+            q2 = z.y;
+        }
+        if (warp < W - 1) {
+            // z_out = Psi z_in + agg; the inclusive scan of lane 31 is agg
+            const float4 Ps = cf->psi_pow[0];
+            const float o1 = fmaf(Ps.x, q1, fmaf(Ps.y, q2, S1));
+            const float o2 = fmaf(Ps.z, q1, fmaf(Ps.w, q2, S2));
+            mbar_publish(&ho->val[k][warp], o1, o2, &ho->bar[k][warp], lane == 31);
+        }
+        Zw = make_float2(q1, q2);
+    }
 
     // fold the warp's true incoming state into this lane's
     const float4 Pl = cf->lane_pow[lane];
@@ -158,8 +265,9 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
 // outgoing state, and each warp's incoming state.
 template <int W>
 __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int64_t t, int64_t ti,
-                                              int64_t nt, uint32_t epoch, const Coef32* cf,
-                                              const CoefDF* cd, SectionShared<W>* sh) {
+                                              int64_t nt, bool carry, uint32_t epoch,
+                                              const Coef32* cf, const CoefDF* cd,
+                                              SectionShared<W>* sh) {
     const int lane = threadIdx.x & 31;
     // everything this section needs, read while the data warps compute
     float4 Pr[4];
@@ -198,7 +306,7 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
     }
     const float C1 = __shfl_sync(0xffffffffu, A1, W - 1);
     const float C2 = __shfl_sync(0xffffffffu, A2, W - 1);
-    const bool has_succ = ti + 1 < nt;
+    const bool has_succ = carry && ti + 1 < nt;
     const Words Wd = section_words(p, k);
     df Z1, Z2;
     if (ti == 0) {
@@ -207,6 +315,11 @@ __device__ __forceinline__ void coord_section(const Params& p, int k, int c, int
         const float q1 = zi1 * gi, q2 = zi2 * gi;
         Z1 = df{q1, fmaf(zi1, gi, -q1)};
         Z2 = df{q2, fmaf(zi2, gi, -q2)};
+    } else if (!carry) {
+        // within the channel's memory horizon: the tile started early enough
+        // for zero state to be exact to far below FP32 rounding
+        Z1 = df{0.f, 0.f};
+        Z2 = df{0.f, 0.f};
     } else {
         if (has_succ && lane == 0) write_agg(Wd, t, (epoch << 2) | kFlagAgg, C1, C2);
         lookback_warp<false>(p, t, ti, k, epoch, cd, Z1, Z2);
@@ -231,6 +344,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     extern __shared__ float4 s_tile4[];
     float* s_tile = reinterpret_cast<float*>(s_tile4);
     __shared__ SectionShared<W> sh;
+    __shared__ HandOff<W> ho;
     __shared__ int64_t s_t;
     // the current channel's coefficient tables, staged once per channel
     __shared__ Coef32 s_c32[kMaxSections];
@@ -245,6 +359,9 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     const uint32_t epoch = *reinterpret_cast<volatile uint32_t*>(&p.hdr->epoch);
     const int64_t total = p.hdr->total_tiles;
     const int64_t nrounds = p.hdr->nrounds;
+    // hand-off barriers (made visible to the CTA by the first loop barrier)
+    for (int i = tid; i < kMaxSections * W; i += blockDim.x) mbar_init(&ho.bar[0][0] + i, 1);
+    uint32_t ph = 0;  // data warps: hand-off barrier parity per section
 
     // final states that no tile writes: sections past K[c] are zero, an
     // empty channel keeps its initial state
@@ -291,9 +408,16 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             ti = d - __ldg(&p.tb[c]);
         }
         const ChanInfo ci = p.chan[c];
-        const int64_t t = __ldg(&p.tb[c]) + ti;  // the tile's slot index (channel-major)
+        const int64_t t = ci.slot + ti;  // the tile's look-back slot
         const int64_t nt = ci.ntiles;
-        const int64_t start = ti * KT::kTile;
+        // Tiles of a channel with memory horizon P >= 0 overlap by P samples:
+        // tile 0 covers [0, T) from zi, tile ti > 0 computes
+        // [T + (ti - 1)(T - P) - P, ...) from zero state and stores all but
+        // its first P samples.  Other channels' tiles abut and carry the state.
+        const bool carry = ci.horizon < 0;
+        const int skip = (!carry && ti > 0) ? ci.horizon : 0;
+        const int64_t start =
+            skip ? KT::kTile + (ti - 1) * (KT::kTile - skip) - skip : ti * KT::kTile;
         const int64_t rem = ci.len - start;
         const int r = (int)(rem < KT::kTile ? rem : KT::kTile);  // valid samples
         const float* src = p.x + ci.off + start;
@@ -323,11 +447,12 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
         __syncthreads();
 
         if (coord) {
-            for (int k = 0; k < ci.K; ++k)
-                coord_section<W>(p, k, c, t, ti, nt, epoch, &s_c32[k], &s_cdf[k], &sh);
+            if (carry)
+                for (int k = 0; k < ci.K; ++k)
+                    coord_section<W>(p, k, c, t, ti, nt, carry, epoch, &s_c32[k], &s_cdf[k], &sh);
         } else {
             float v[N];
-            const int chunk = (warp - 1) * 32 + lane;
+            const int chunk = (W - warp) * 32 + lane;  // group W - warp of the tile
 #pragma unroll
             for (int g = 0; g < N / 4; ++g) {
                 const float4 q = s_tile4[S::g(chunk * (N / 4) + g)];
@@ -345,16 +470,32 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             // while the sections run (plain layout, only that lane touches it)
             float* s_own = s_tile + chunk * N;
             if (ci.mode) {
-                for (int k = 0; k < ci.K; ++k)
-                    data_section<N, W, true>(p, v, k, c, t, ti, epoch, &s_c32[k], &s_cdf[k], &sh,
-                                             zf_owner, mq, s_own);
+                if (carry) {
+                    for (int k = 0; k < ci.K; ++k)
+                        data_section<N, W, true, false>(p, v, k, c, t, ti, epoch, &s_c32[k],
+                                                        &s_cdf[k], &sh, zf_owner, mq, s_own, &ho,
+                                                        ph);
+                } else {
+                    for (int k = 0; k < ci.K; ++k)
+                        data_section<N, W, true, true>(p, v, k, c, t, ti, epoch, &s_c32[k],
+                                                       &s_cdf[k], &sh, zf_owner, mq, s_own, &ho,
+                                                       ph);
+                }
                 const float G = s_c32[ci.K - 1].misc.y;
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] *= G;
             } else {
-                for (int k = 0; k < ci.K; ++k)
-                    data_section<N, W, false>(p, v, k, c, t, ti, epoch, &s_c32[k], &s_cdf[k], &sh,
-                                              zf_owner, mq, s_own);
+                if (carry) {
+                    for (int k = 0; k < ci.K; ++k)
+                        data_section<N, W, false, false>(p, v, k, c, t, ti, epoch, &s_c32[k],
+                                                         &s_cdf[k], &sh, zf_owner, mq, s_own, &ho,
+                                                         ph);
+                } else {
+                    for (int k = 0; k < ci.K; ++k)
+                        data_section<N, W, false, true>(p, v, k, c, t, ti, epoch, &s_c32[k],
+                                                        &s_cdf[k], &sh, zf_owner, mq, s_own, &ho,
+                                                        ph);
+                }
             }
             // S7: registers -> shared (swizzled)
             __syncwarp();  // order the zf owner's scratch writes before the lanes' stores
@@ -364,14 +505,16 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
                     make_float4(v[4 * g + 0], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
         }
         __syncthreads();
-        // shared -> global, all W + 1 warps
+        // shared -> global, all W + 1 warps (the first `skip` samples are
+        // the overlap, already stored by the previous tile; skip % 16 == 0)
         float* dst = p.y + ci.off + start;
         if (((reinterpret_cast<uintptr_t>(dst) & 15u) == 0) && r == KT::kTile) {
             float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll 4
-            for (int g = tid; g < KT::kGran; g += KT::kThreads) __stcs(d4 + g, s_tile4[S::g(g)]);
+            for (int g = (skip >> 2) + tid; g < KT::kGran; g += KT::kThreads)
+                __stcs(d4 + g, s_tile4[S::g(g)]);
         } else {
-            for (int j = tid; j < r; j += KT::kThreads) __stcs(dst + j, s_tile[S::e(j)]);
+            for (int j = skip + tid; j < r; j += KT::kThreads) __stcs(dst + j, s_tile[S::e(j)]);
         }
         __syncthreads();
     }
@@ -410,7 +553,7 @@ struct KernelEntry {
 static const KernelEntry kEntries[] = {
     SOSF_ENTRY(16, 8, 3),  SOSF_ENTRY(16, 16, 2), SOSF_ENTRY(32, 4, 4), SOSF_ENTRY(32, 7, 3),
     SOSF_ENTRY(32, 8, 2),  SOSF_ENTRY(32, 16, 1), SOSF_ENTRY(64, 3, 4), SOSF_ENTRY(64, 4, 2),
-    SOSF_ENTRY(64, 8, 1),
+    SOSF_ENTRY(64, 8, 1),  SOSF_ENTRY(64, 7, 2),
 };
 
 bool forward_supported(int N, int W) {

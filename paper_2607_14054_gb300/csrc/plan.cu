@@ -1,9 +1,12 @@
 // Plan kernel: per-call set-up of the workspace, entirely on the device so
 // that a call never synchronises and can be captured into a CUDA graph.
 //
-//  * block C (the last one): channel offsets and tile prefix (exclusive scans
-//    of the lengths) and the status word;
-//  * block c < C: the coefficient tables of channel c, one warp per section.
+//  * block C (the last one): channel offsets and look-back slots (exclusive
+//    scans of the lengths and of ceil(len / T)) and the status word;
+//  * block c < C: the coefficient tables of channel c, one warp per section,
+//    and (a ninth warp) the channel's memory horizon and tile count;
+//  * order_kernel, after both: the dispatch prefix over the tile counts and,
+//    when some channel carries its state by look-back, the interleaved order.
 //
 // Coefficient tables (paper Sec. VI-B, "pre-computed before filtering"):
 // the rows are normalised by a0; when every b0 of the channel is nonzero the
@@ -39,15 +42,155 @@ __device__ __forceinline__ bool finite_row(const double* r) {
     return true;
 }
 
-// Blocks 0..C-1: coefficients.  Block C: channel table.  256 threads.
-__global__ void __launch_bounds__(256) plan_kernel(Params p) {
+constexpr int kPlanWarps = kMaxSections + 1;  // one per section + the horizon warp
+constexpr int kPlanThreads = kPlanWarps * 32;
+
+// complex FP32 helpers for the horizon bound
+struct cpx {
+    float re, im;
+};
+__device__ __forceinline__ cpx cmul(cpx a, cpx b) {
+    return cpx{fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re)};
+}
+__device__ __forceinline__ cpx cdiv(cpx a, cpx b) {
+    const float d = fmaf(b.re, b.re, b.im * b.im);
+    return cpx{fmaf(a.re, b.re, a.im * b.im) / d, fmaf(a.im, b.re, -a.re * b.im) / d};
+}
+__device__ __forceinline__ float cabs_(cpx a) { return hypotf(a.re, a.im); }
+
+// Memory horizon of one channel (one warp; rows[k] = normalised b0, b1, b2,
+// a1, a2 of section k).  The cascade's impulse response is, past its first
+// 2K samples, h[n] = sum_i R_i p_i^n over the nonzero poles p_i (partial
+// fractions of prod_k B_k(z) / A_k(z), distinct poles), so its absolute tail
+// from n on is at most sum_i |R_i| |p_i|^n / (1 - |p_i|).  A tile that starts
+// P samples early from zero state drops exactly such a tail of the input's
+// convolution; P is the smallest multiple of 16 (and >= 2K) for which each
+// pole's share is below kHorizonEps * ||h||_2 / (2K), with ||h||_2 bounded
+// from below by half the norm of the first 64 samples (filtered here in
+// FP32).  The initial state's response (DF2T state (k, j) responds with
+// z^-j / A_k(z) * prod_{m > k} B_m / A_m) must likewise have decayed below
+// the bound at the end of the first tile.  Returns -1 when no such P <= T / 2
+// exists, when a pole lies on or outside |z| = 1 - 1e-7, or when two poles
+// are closer than 1e-4 (relative), where the partial fractions are not
+// reliable.
+__device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int lane, cpx* s_pole) {
+    // ||h||_2 lower bound: lane 0 filters a unit impulse for 64 samples
+    float e2 = 0.f;
+    if (lane == 0) {
+        float z1[kMaxSections], z2[kMaxSections];
+#pragma unroll
+        for (int k = 0; k < kMaxSections; ++k) z1[k] = z2[k] = 0.f;
+        for (int n = 0; n < 64; ++n) {
+            float u = n == 0 ? 1.f : 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxSections; ++k) {
+                if (k < K) {
+                    const float b0 = (float)rows[k][0], b1 = (float)rows[k][1],
+                                b2 = (float)rows[k][2], a1 = (float)rows[k][3],
+                                a2 = (float)rows[k][4];
+                    const float y = fmaf(b0, u, z1[k]);
+                    z1[k] = fmaf(b1, u, fmaf(-a1, y, z2[k]));
+                    z2[k] = fmaf(b2, u, -a2 * y);
+                    u = y;
+                }
+            }
+            e2 = fmaf(u, u, e2);
+        }
+    }
+    const float h2 = 0.5f * sqrtf(__shfl_sync(0xffffffffu, e2, 0));
+    const int np = 2 * K;
+    // poles: lane i < 2K takes root (i & 1) of z^2 + a1 z + a2 of section i / 2
+    if (lane < np) {
+        const double a1 = rows[lane >> 1][3], a2 = rows[lane >> 1][4];
+        const double disc = a1 * a1 - 4.0 * a2;
+        cpx z;
+        if (disc < 0.0) {
+            const double im = 0.5 * sqrt(-disc);
+            z = cpx{(float)(-0.5 * a1), (float)((lane & 1) ? -im : im)};
+        } else {
+            const double sq = sqrt(disc);
+            z = cpx{(float)(0.5 * ((lane & 1) ? -a1 - sq : -a1 + sq)), 0.f};
+        }
+        s_pole[lane] = z;
+    }
+    __syncwarp();
+    bool bad = !(h2 > 0.f);
+    float ptail = 0.f, zsum = 0.f;
+    const float budget = kHorizonEps * h2;
+    if (lane < np && !bad) {
+        const cpx pi = s_pole[lane];
+        const float r = cabs_(pi);
+        if (r > 1e-20f) {
+            if (!(r < 1.f - 1e-7f)) bad = true;
+            const cpx inv = cdiv(cpx{1.f, 0.f}, pi);
+            const cpx inv2 = cmul(inv, inv);
+            // section numerators at p_i (z^-1 = 1 / p_i)
+            cpx Bk[kMaxSections];
+#pragma unroll
+            for (int m = 0; m < kMaxSections; ++m) {
+                Bk[m] = cpx{1.f, 0.f};
+                if (m < K) {
+                    const float b0 = (float)rows[m][0], b1 = (float)rows[m][1],
+                                b2 = (float)rows[m][2];
+                    Bk[m] = cpx{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)),
+                                fmaf(b2, inv2.im, b1 * inv.im)};
+                }
+            }
+            // walk the sections from the last to the first: den = prod over
+            // the poles of sections >= k (except p_i) of (1 - p_l / p_i),
+            // num = prod_{m > k} B_m(p_i)
+            cpx num{1.f, 0.f}, den{1.f, 0.f};
+            float rz = 0.f;
+            const int own = lane >> 1;
+            for (int k = K - 1; k >= 0; --k) {
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int l = 2 * k + q;
+                    if (l != lane) {
+                        const cpx f = cdiv(s_pole[l], pi);
+                        const cpx g = cpx{1.f - f.re, -f.im};
+                        if (cabs_(g) < 1e-4f) bad = true;
+                        den = cmul(den, g);
+                    }
+                }
+                if (k <= own) {
+                    // state (k, 0) and (k, 1): residue num / den, times 1 / p_i for j = 1
+                    const float a = cabs_(num) / cabs_(den);
+                    rz = fmaxf(rz, a * fmaxf(1.f, 1.f / r));
+                }
+                num = cmul(num, Bk[k]);
+            }
+            // full cascade: num = prod_m B_m(p_i), den over all other poles
+            const float R = cabs_(num) / cabs_(den);
+            if (R > 0.f) {
+                const float n = logf(budget * (1.f - r) / ((float)np * R)) / logf(r);
+                ptail = fmaxf(ptail, n);
+            }
+            zsum = rz * powf(r, (float)T) / (1.f - r);
+            if (!(ptail < 1e9f) || !(zsum < 1e30f)) bad = true;
+        }
+    }
+    // warp reductions
+    for (int o = 16; o > 0; o >>= 1) {
+        ptail = fmaxf(ptail, __shfl_xor_sync(0xffffffffu, ptail, o));
+        zsum += __shfl_xor_sync(0xffffffffu, zsum, o);
+    }
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad || !(zsum <= budget)) return -1;
+    const float need = fmaxf(ptail, (float)np);
+    const int64_t P = ((int64_t)ceilf(need) + 15) / 16 * 16;
+    return P <= T / 2 ? (int)P : -1;
+}
+
+// Blocks 0..C-1: coefficients and horizon.  Block C: channel table.
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int C = p.C, kmax = p.kmax;
 
     if ((int)blockIdx.x == C) {
-        // ---- channel table: exclusive scans of lengths and tile counts ----
+        // ---- channel table: exclusive scans of lengths and slot counts ----
         const int64_t T = (int64_t)p.W * kLanes * p.N;
-        __shared__ int64_t s_wsum_len[8], s_wsum_til[8];
+        __shared__ int64_t s_wsum_len[kPlanWarps], s_wsum_til[kPlanWarps];
         __shared__ int64_t s_carry_len, s_carry_til;
         if (tid == 0) {
             s_carry_len = 0;
@@ -56,7 +199,7 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
             p.hdr->nchan = C;
         }
         __syncthreads();
-        for (int base = 0; base < C; base += 256) {
+        for (int base = 0; base < C; base += kPlanThreads) {
             const int c = base + tid;
             int64_t len = 0, nt = 0;
             int32_t K = 0;
@@ -92,26 +235,20 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
             }
             const int64_t cl = s_carry_len, ct = s_carry_til;
             if (c < C) {
-                // mode and err belong to the coefficient block of channel c
+                // mode, err, horizon and ntiles belong to the coefficient block
                 p.chan[c].off = cl + wl + il - len;
                 p.chan[c].len = len;
                 p.chan[c].K = K;
-                p.chan[c].ntiles = (int32_t)nt;
-                p.tb[c] = ct + wt + it - nt;
+                p.chan[c].slot = ct + wt + it - nt;
             }
             __syncthreads();
-            if (tid == 255) {
+            if (tid == kPlanThreads - 1) {
                 s_carry_len = cl + wl + il;
                 s_carry_til = ct + wt + it;
             }
             __syncthreads();
         }
-        if (tid == 0) {
-            const int64_t total = s_carry_til;
-            p.tb[C] = total;
-            if (total > p.cap_tiles) set_status(p.hdr, SOS_ERR_WORKSPACE);
-            p.hdr->total_tiles = total > p.cap_tiles ? 0 : total;
-        }
+        if (tid == 0 && s_carry_til > p.cap_tiles) set_status(p.hdr, SOS_ERR_WORKSPACE);
         return;
     }
 
@@ -120,6 +257,8 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     __shared__ double s_b0[kMaxSections];
     __shared__ int s_mode;
     __shared__ double s_G[kMaxSections];
+    __shared__ double s_row[kMaxSections][5];
+    __shared__ cpx s_pole[2 * kMaxSections];
     // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
     __shared__ dfm2 s_chain[kMaxSections][20];
 
@@ -143,6 +282,13 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     const double ia0 = 1.0 / row[3];
     const double b0 = row[0] * ia0, b1 = row[1] * ia0, b2 = row[2] * ia0;
     const double a1 = row[4] * ia0, a2 = row[5] * ia0;
+    if (lane == 0 && k < kMaxSections) {
+        s_row[k][0] = b0;
+        s_row[k][1] = b1;
+        s_row[k][2] = b2;
+        s_row[k][3] = a1;
+        s_row[k][4] = a2;
+    }
     if (active && (p.flags_opt & SOS_FLAG_CHECK_STABLE)) {
         // both roots of z^2 + a1 z + a2 strictly inside the unit circle
         // (Jury: |a2| < 1 and |a1| < 1 + a2)
@@ -171,6 +317,23 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     __syncthreads();
     const int mode = s_mode;
 
+    if (warp == kMaxSections) {
+        // the horizon warp: memory horizon and tile count of channel c
+        const int64_t T = (int64_t)p.W * kLanes * p.N;
+        const int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY) ? -1
+                                                           : channel_horizon(s_row, Kc, T, lane, s_pole);
+        if (lane == 0) {
+            int64_t len = p.lengths[c];
+            if (len < 0) len = 0;
+            int64_t nt;
+            if (len == 0) nt = 0;
+            else if (P >= 0 && len > T) nt = 1 + (len - T + (T - P) - 1) / (T - P);
+            else nt = (len + T - 1) / T;
+            p.chan[c].horizon = P;
+            p.chan[c].ntiles = (int32_t)nt;
+        }
+        return;
+    }
     if (!active) return;
 
     // ---- double-float squaring chain (lane 0) ----
@@ -231,21 +394,59 @@ __global__ void __launch_bounds__(256) plan_kernel(Params p) {
     }
 }
 
-// Interleaved dispatch order (one CTA of 1024 threads, runs after
-// plan_kernel).  Tiles are handed out round by round: round r holds tile r of
-// every channel that has more than r tiles.  Then a tile's predecessor in its
-// own channel was dispatched a whole round earlier and has usually finished,
-// so the look-back finds its outgoing state at once.  Channels are sorted by
+// Dispatch (one CTA of 1024 threads, runs after plan_kernel).  First the
+// tile prefix tb over the channels' tile counts.  Then, when some channel
+// with more than one tile carries its state by look-back, the interleaved
+// order: tiles are handed out round by round, round r holding tile r of every
+// channel that has more than r tiles, so that a tile's predecessor in its own
+// channel was dispatched a whole round earlier and has usually finished and
+// the look-back finds its outgoing state at once.  Channels are sorted by
 // decreasing tile count (bitonic sort in shared memory), which makes each
-// round a prefix of that order.  With more than kMaxSortChannels channels the
-// kernel leaves nrounds = 0 and tiles go channel by channel.
+// round a prefix of that order.  Otherwise (every channel within its memory
+// horizon, or more than kMaxSortChannels channels) nrounds = 0 and tiles go
+// channel by channel, which keeps a tile's overlap with its predecessor in L2.
 __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     extern __shared__ unsigned long long s_key[];
     const int tid = threadIdx.x, C = p.C;
-    if (C > kMaxSortChannels) {
-        if (tid == 0) p.hdr->nrounds = 0;
-        return;
+    const int lane = tid & 31, warp = tid >> 5;
+    __shared__ int64_t s_carry;
+    __shared__ int64_t s_wsum[32];
+    // ---- tile prefix ----
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    int carried = 0;
+    for (int base = 0; base < C; base += blockDim.x) {
+        const int c = base + tid;
+        int64_t nt = 0;
+        if (c < C) {
+            const ChanInfo ci = p.chan[c];
+            nt = ci.ntiles;
+            if (ci.horizon < 0 && nt > 1) carried = 1;
+        }
+        int64_t inc = nt;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) s_wsum[warp] = inc;
+        __syncthreads();
+        int64_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
+        const int64_t carry = s_carry;
+        if (c < C) p.tb[c] = carry + wpre + inc - nt;
+        __syncthreads();
+        if (tid == blockDim.x - 1) s_carry = carry + wpre + inc;
+        __syncthreads();
     }
+    const int64_t total = s_carry;
+    const bool interleave = __syncthreads_or(carried) != 0 && C <= kMaxSortChannels;
+    if (tid == 0) {
+        p.tb[C] = total;
+        p.hdr->total_tiles = p.hdr->status == SOS_ERR_WORKSPACE ? 0 : total;
+        if (!interleave) p.hdr->nrounds = 0;
+    }
+    if (!interleave) return;
+    __syncthreads();
     int n = 1;
     while (n < C) n <<= 1;
     for (int i = tid; i < n; i += blockDim.x) {
@@ -274,11 +475,8 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     for (int i = tid; i < C; i += blockDim.x) p.order[i] = (int32_t)(s_key[i] & 0xffffffffu);
     const int64_t nrounds = C > 0 ? (int64_t)(0xffffffffull - (s_key[0] >> 32)) : 0;
     // rp[r] = sum over rounds q < r of (channels with more than q tiles)
-    __shared__ int64_t s_carry;
-    __shared__ int64_t s_wsum[32];
     if (tid == 0) s_carry = 0;
     __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5;
     for (int64_t base = 0; base <= nrounds; base += blockDim.x) {
         const int64_t r = base + tid;
         int64_t cnt = 0;
@@ -314,7 +512,7 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
 
 namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream) {
-    plan_kernel<<<p.C + 1, 256, 0, stream>>>(p);
+    plan_kernel<<<p.C + 1, kPlanThreads, 0, stream>>>(p);
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     int n = 1;

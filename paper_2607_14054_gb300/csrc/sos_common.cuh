@@ -44,13 +44,28 @@ struct WsHeader {
 static_assert(sizeof(WsHeader) == 64, "header size");
 
 struct ChanInfo {
-    int64_t off;     // first sample of the channel in the packed arrays
-    int64_t len;     // samples
-    int32_t K;       // sections used
-    int32_t mode;    // 1: b0 factored out of every section (Sec. II, Eq. simple_second_order)
-    int32_t ntiles;  // tiles of this channel
-    int32_t err;     // coefficient error found by the plan kernel (sos_status), 0 if none
+    int64_t off;      // first sample of the channel in the packed arrays
+    int64_t len;      // samples
+    int32_t K;        // sections used
+    int32_t mode;     // 1: b0 factored out of every section (Sec. II, Eq. simple_second_order)
+    int32_t ntiles;   // tiles of this channel (dispatch)
+    int32_t err;      // coefficient error found by the plan kernel (sos_status), 0 if none
+    int64_t slot;     // first look-back slot of the channel (ceil(len / T) slots)
+    int32_t horizon;  // >= 0: memory horizon P (tiles overlap by P samples, no carry);
+                      // -1: the state is carried by the look-back
+    int32_t pad;
 };
+static_assert(sizeof(ChanInfo) == 48, "channel table entry");
+
+// A channel's memory horizon P is the shortest warm-up after which the
+// cascade's impulse-response tail, summed in absolute value, is below
+// kHorizonEps times a lower bound of the response's L2 norm (and the
+// initial state's contribution past the first tile is below the same
+// bound).  Tiles of such a channel start P samples early from zero state;
+// the state they drop changes the output by less than kHorizonEps relative,
+// far below FP32 rounding.  Longer memories (P > T / 2, poles on or near the
+// unit circle, coincident poles) keep the decoupled look-back.
+constexpr float kHorizonEps = 0x1p-30f;
 
 // Per (channel, section) FP32 coefficients and transition-matrix powers.
 // The DF2T state transition of one sample is A = [[-a1, 1], [-a2, 0]];
@@ -99,7 +114,9 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.chan = o;  o = align_up(o + sizeof(ChanInfo) * (size_t)C, 256);
     L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
     L.order = o; o = align_up(o + sizeof(int32_t) * (size_t)C, 256);
-    L.rp = o;    o = align_up(o + sizeof(int64_t) * ((size_t)(cap_tiles > 0 ? cap_tiles : 0) + 2), 256);
+    // rounds of the interleaved dispatch: at most the longest channel's tile
+    // count, which overlapping tiles (stride >= T / 2) at most double
+    L.rp = o;    o = align_up(o + sizeof(int64_t) * (2 * (size_t)(cap_tiles > 0 ? cap_tiles : 0) + 2), 256);
     L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
     L.cdf = o;   o = align_up(o + sizeof(CoefDF) * (size_t)C * kmax, 256);
     const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);

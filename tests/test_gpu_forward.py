@@ -207,3 +207,98 @@ def test_batched_full_size_sampled_channels():
     ys = np.concatenate([y[off[c]:off[c + 1]] for c in pick])
     err = check(ys, zf[pick], y_ref, zf_ref, ls.numpy(), wl.K[pick].cpu().numpy(), 1e-5)
     print("batched rel-L2 max", float(err.max()), "median", float(np.median(err)))
+
+
+@pytest.mark.parametrize("N,W", [(32, 8), (16, 16), (64, 4), (32, 7)])
+def test_ragged_multichannel_carry_only(N, W):
+    """The same ragged cases with every channel's state carried by the
+    look-back (no overlapping tiles)."""
+    T = N * 32 * W
+    lengths = [1, T - 1, T, T + 1, 3 * T + 5, 0, 7 * T + 333, 2 * T]
+    args = random_case(200 + N + W, lengths, 8)
+    y_ref, zf_ref = run_oracle(*args)
+    y, zf = run_gpu(args, tuning=(N, W, 0, 2))
+    check(y, zf, y_ref, zf_ref, np.array(lengths), args[2].numpy(), 1e-5)
+
+
+def _impulse_response(sos_c, n):
+    x = np.zeros(n)
+    x[0] = 1.0
+    y, _ = oracle.sosfilt(x, sos_c[None], K=np.array([len(sos_c)]), lengths=np.array([n]))
+    return y
+
+
+def test_horizons_bound_the_true_impulse_tail():
+    """Every horizon P >= 0 the plan picks leaves an impulse-response tail
+    sum_{n >= P} |h[n]| below 2^-30 ||h||_2 (the state a tile drops changes
+    its output by at most that, relative), computed here from the oracle's
+    FP64 impulse response; coincident poles and near-unit-circle poles get
+    P = -1 (carried by the look-back)."""
+    P = _lib()
+    from synth import filters
+    C = 72
+    kmax = 8
+    K = np.array([8] * 64 + [8, 2, 1, 3, 2, 8, 4, 8], dtype=np.int32)
+    sos = np.zeros((C, kmax, 6))
+    sos[:, :, 0] = 1.0
+    sos[:, :, 3] = 1.0
+    sos[:64] = workloads._random_bank(31, 64, kmax, 0.5, 0.995, K[:64])
+    sos[64] = workloads.plain_bandpass16(n=16).sos.numpy()[0]
+    sos[65, :2] = workloads.plain_lowpass(n=16).sos.numpy()[0, 0]        # two equal sections
+    sos[66, 0] = [0.5, 0.25, 0.0, 1.0, -0.9, 0.0]                       # first order, pole 0.9
+    sos[67, :3] = [[1.0, 0.5, 0.25, 1.0, 0.0, 0.0],                     # pure FIR section
+                   [0.3, 0.0, 0.0, 1.0, -0.5, 0.06],                    # real poles 0.2, 0.3
+                   [1.0, -1.0, 0.0, 2.0, -1.0, 0.4]]                    # a0 = 2
+    sos[68, :2] = filters.random_sections(32, 2, 0.999, 0.9999)        # long memory
+    sos[69] = workloads._random_bank(33, 1, kmax, 0.98, 0.995, np.array([8]))[0]
+    sos[70, :4] = filters.random_sections(34, 4, 0.2, 0.6)
+    sos[71] = workloads._random_bank(35, 1, kmax, 0.9, 0.97, np.array([8]))[0]
+    lengths = torch.full((C,), 50_000, dtype=torch.int64)
+    plan = P.SosFilter(lengths, kmax)
+    plan.prepare(torch.from_numpy(sos).cuda(), torch.from_numpy(K).cuda())
+    hz, tiles = plan.plan_info()
+    hz, tiles = hz.numpy(), tiles.numpy()
+    T = 32 * 32 * 8
+    assert hz[65] == -1 and hz[68] == -1
+    for c in range(C):
+        L = 50_000
+        if hz[c] < 0:
+            assert tiles[c] == -(-L // T)
+            continue
+        assert hz[c] % 16 == 0 and 2 * int(K[c]) <= hz[c] <= T // 2
+        assert tiles[c] == 1 + -(-(L - T) // (T - hz[c]))
+        h = _impulse_response(sos[c, :K[c]], 1 << 17)
+        tail = np.abs(h[hz[c]:]).sum()
+        assert tail <= 2.0 ** -30 * np.sqrt((h ** 2).sum()), (c, hz[c], tail)
+    # at T = 8192 a few of the slowest-decaying random cascades (radius up to
+    # 0.995) need more than T / 2 and are carried instead
+    assert (hz[:64] >= 0).mean() >= 0.85, hz[:64]
+
+
+def test_long_and_short_memory_channels_in_one_batch():
+    """Channels with poles at radius 0.999..0.9999 (carried by the look-back,
+    stress tolerance 1e-3) batched with short-memory channels (overlapping
+    tiles, 1e-5), interleaved dispatch."""
+    P = _lib()
+    from synth import filters
+    lengths = [300_000, 120_000, 250_000, 90_000, 400_000, 7]
+    C, kmax = len(lengths), 8
+    K = np.array([8, 6, 8, 3, 8, 2], dtype=np.int32)
+    sos = np.zeros((C, kmax, 6))
+    sos[:, :, 0] = 1.0
+    sos[:, :, 3] = 1.0
+    for c, k in enumerate(K):
+        rmin, rmax = (0.999, 0.9999) if c % 2 == 0 else (0.5, 0.95)
+        sos[c, :k] = filters.random_sections(40 + c, int(k), rmin, rmax)
+    x = rng.normal(41, rng.STREAM_SIGNAL, sum(lengths))
+    zi = rng.normal(41, rng.STREAM_STATE, C * kmax * 2).view(C, kmax, 2)
+    args = (x, torch.from_numpy(sos), torch.from_numpy(K), torch.tensor(lengths), zi)
+    y, zf = run_gpu(args)
+    plan = P.SosFilter(torch.tensor(lengths), kmax)
+    plan.prepare(args[1].cuda(), args[2].cuda())
+    hz, _ = plan.plan_info()
+    assert (hz.numpy()[0:5:2] == -1).all() and (hz.numpy()[1::2] >= 0).all()
+    y_ref, zf_ref = run_oracle(*args)
+    err = oracle.rel_l2_per_channel(y, y_ref, np.array(lengths))
+    print("long-memory rel-L2", err[0:5:2], "short", err[1::2])
+    assert err[1::2].max() <= 1e-5 and err[0:5:2].max() <= 1e-3
