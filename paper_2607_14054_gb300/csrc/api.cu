@@ -7,7 +7,9 @@
 namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream);
 cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream);
+cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream);
 bool forward_supported(int N, int W);
+bool pipe_supported(int N);
 }  // namespace sosf
 
 using namespace sosf;
@@ -29,9 +31,35 @@ bool resolve_tuning(const sos_tuning* t, Tune* out) {
         r.flags = t->flags;
     }
     if (r.algo != 1) return false;
-    if (!forward_supported(r.N, r.W)) return false;
+    if (!forward_supported(r.N, r.W) || !pipe_supported(r.N)) return false;
     *out = r;
     return true;
+}
+
+// SMs of the current device (cached per device); 0 if unknown.
+int device_sms() {
+    static int s_sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (s_sms[dev] == 0 &&
+        cudaDeviceGetAttribute(&s_sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return s_sms[dev];
+}
+
+constexpr int kPipeCtasPerSm = 2;
+
+// Pipeline segment length: long enough that the warm-up before each segment
+// is a small fraction of it, short enough that the segments of the whole
+// call keep every pipeline CTA busy (between 8 and 64 groups of 32 N).
+int64_t segment_length(int64_t total_len, int N) {
+    const int64_t group = 32LL * N;
+    const int sms = device_sms();
+    const int64_t ctas = (int64_t)(sms > 0 ? sms : 148) * kPipeCtasPerSm;
+    int64_t g = (total_len + ctas * group - 1) / (ctas * group);
+    if (g < 8) g = 8;
+    if (g > 64) g = 64;
+    return g * group;
 }
 
 int64_t count_tiles(int32_t C, const int64_t* lengths_host, int64_t T, bool* ok) {
@@ -111,6 +139,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->hdr = reinterpret_cast<WsHeader*>(ws + L.hdr);
     p->chan = reinterpret_cast<ChanInfo*>(ws + L.chan);
     p->tb = reinterpret_cast<int64_t*>(ws + L.tb);
+    p->tbp = reinterpret_cast<int64_t*>(ws + L.tbp);
     p->order = reinterpret_cast<int32_t*>(ws + L.order);
     p->rp = reinterpret_cast<int64_t*>(ws + L.rp);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
@@ -122,6 +151,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->N = tu.N;
     p->W = tu.W;
     p->flags_opt = tu.flags;
+    p->seg = segment_length(total_len, tu.N);
     *tiles_out = tiles;
     *total_len_out = total_len;
     return SOS_OK;
@@ -166,7 +196,14 @@ sos_status sos_apply(const float* x, int32_t n_channels, int32_t kmax,
     p.y = y;
     p.zi = zi;
     p.zf = zf;
-    // at least one CTA so that final states of empty channels get written
+    // the section pipeline for channels within their memory horizon, then
+    // the look-back kernel for the others (which also writes the final states
+    // of empty channels and unused sections: at least one CTA)
+    if (total > 0) {
+        const int64_t grid = (int64_t)(device_sms() > 0 ? device_sms() : 1) * kPipeCtasPerSm;
+        if (launch_pipe(p, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+            return SOS_ERR_CUDA;
+    }
     const int64_t launch_tiles = tiles > 0 ? tiles : 1;
     if (launch_forward(p, launch_tiles, static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return SOS_ERR_CUDA;

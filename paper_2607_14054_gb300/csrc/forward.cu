@@ -37,6 +37,7 @@
 //  S8  the lane holding a channel's last sample writes zf.
 #include <cmath>
 
+#include "sos_async.cuh"
 #include "sos_kernels.cuh"
 
 namespace sosf {
@@ -47,8 +48,77 @@ struct FwdKernel {
     static constexpr int kThreads = (W + 1) * 32;  // W data warps + 1 coordinator warp
     static constexpr int kTile = W * 32 * N;
     static constexpr int kGran = kTile / 4;
-    static constexpr size_t kSmem = sizeof(float) * kTile;
+    static constexpr size_t kSmem = 2 * sizeof(float) * kTile;  // two tile buffers
 };
+
+// Where a dispatched tile lies.  Tiles of a channel with memory horizon
+// P >= 0 overlap by P samples: tile 0 covers [0, T) from zi, tile ti > 0
+// computes [T + (ti - 1)(T - P) - P, ...) from zero state and stores all but
+// its first P samples.  Other channels' tiles abut and carry the state.
+struct TileGeom {
+    int64_t ti, t, nt, start;  // index in channel, look-back slot, channel tiles, first sample
+    const float* src;          // x of the first sample
+    int c, r, skip;            // channel, valid samples, overlap samples not stored
+    bool carry;
+};
+
+template <int kTile>
+__device__ __forceinline__ TileGeom tile_geom(const Params& p, int64_t d, int64_t nrounds) {
+    int c;
+    int64_t ti;
+    if (nrounds > 0) {
+        // interleaved: round r = the largest with rp[r] <= d, then the
+        // (d - rp[r])-th channel of the sorted order
+        int64_t lo = 0, hi = nrounds - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.rp[mid]) <= d) lo = mid; else hi = mid - 1;
+        }
+        ti = lo;
+        c = __ldg(&p.order[d - __ldg(&p.rp[lo])]);
+    } else {
+        // channel by channel: the largest c with tb[c] <= d
+        int lo = 0, hi = p.C - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(&p.tb[mid]) <= d) lo = mid; else hi = mid - 1;
+        }
+        c = lo;
+        ti = d - __ldg(&p.tb[c]);
+    }
+    const ChanInfo ci = p.chan[c];
+    TileGeom g;
+    g.c = c;
+    g.ti = ti;
+    g.t = ci.slot + ti;
+    g.nt = ci.ntiles;
+    g.carry = ci.horizon < 0;
+    g.skip = (!g.carry && ti > 0) ? ci.horizon : 0;
+    g.start = g.skip ? kTile + (ti - 1) * (kTile - g.skip) - g.skip : ti * kTile;
+    const int64_t rem = ci.len - g.start;
+    g.r = (int)(rem < kTile ? rem : kTile);
+    g.src = p.x + ci.off + g.start;
+    return g;
+}
+
+
+// S2, issued one tile ahead: global -> shared (swizzled) by asynchronous
+// copies, zero beyond the channel end; all W + 1 warps take part.
+template <int N, int W>
+__device__ __forceinline__ void issue_tile_load(const TileGeom& g, float4* buf4, int tid) {
+    using KT = FwdKernel<N, W>;
+    using S = Swz<N>;
+    const bool vec = ((reinterpret_cast<uintptr_t>(g.src) & 15u) == 0) && g.r == KT::kTile;
+    if (vec) {
+        const float4* s4 = reinterpret_cast<const float4*>(g.src);
+#pragma unroll 4
+        for (int q = tid; q < KT::kGran; q += KT::kThreads) cp_async16(buf4 + S::g(q), s4 + q);
+    } else {
+        float* buf = reinterpret_cast<float*>(buf4);
+        for (int j = tid; j < KT::kTile; j += KT::kThreads)
+            cp_async4(buf + S::e(j), j < g.r ? g.src + j : g.src, j < g.r);
+    }
+}
 
 // Per-section shared state between the data warps and the coordinator.
 template <int W>
@@ -71,46 +141,6 @@ struct HandOff {
     unsigned long long bar[kMaxSections][W];
 };
 
-__device__ __forceinline__ unsigned smem_u32(const void* a) {
-    return (unsigned)__cvta_generic_to_shared(a);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(
-                     smem_u32(b))
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* b, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Store of the hand-off value and arrive, both predicated on `pred` inside
-// the asm block (no branch, so the warp stays converged).
-__device__ __forceinline__ void mbar_publish(float2* v, float a, float b, unsigned long long* bar,
-                                             bool pred) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b64 st;\n\tsetp.ne.u32 p, %4, 0;\n\t"
-        "@p st.shared.v2.f32 [%0], {%1, %2};\n\t"
-        "@p mbarrier.arrive.shared::cta.b64 st, [%3];\n\t}" ::"r"(smem_u32(v)),
-        "f"(a), "f"(b), "r"(smem_u32(bar)), "r"((unsigned)pred)
-        : "memory");
-}
-
-// bound on try_wait calls in one hand-off (each call may suspend the warp
-// for a while before returning false)
-constexpr uint32_t kHandOffLimit = 1u << 20;
 
 // One section of the cascade on a data warp's register-resident chunk.
 // CHAIN = false: the warp's incoming state comes from the coordinator warp
@@ -342,7 +372,6 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     using KT = FwdKernel<N, W>;
     using S = Swz<N>;
     extern __shared__ float4 s_tile4[];
-    float* s_tile = reinterpret_cast<float*>(s_tile4);
     __shared__ SectionShared<W> sh;
     __shared__ HandOff<W> ho;
     __shared__ int64_t s_t;
@@ -379,48 +408,41 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
         }
     }
 
-    for (;;) {
+    // Tiles are reserved one ahead: while tile d computes from one buffer,
+    // the copies of the next reserved tile fill the other.  A CTA still
+    // processes its tiles in dispatch order, and the lowest unfinished tile
+    // is always some CTA's current one, so the look-back keeps progressing.
+    if (tid == 0) s_t = (int64_t)atomicAdd(&p.hdr->tile_counter, 1u);
+    __syncthreads();
+    int64_t d = s_t;
+    TileGeom gc{};
+    if (d < total) {
+        gc = tile_geom<KT::kTile>(p, d, nrounds);
+        issue_tile_load<N, W>(gc, s_tile4, tid);
+    }
+    cp_async_commit();
+    int cur = 0;
+    while (d < total) {
         if (tid == 0) s_t = (int64_t)atomicAdd(&p.hdr->tile_counter, 1u);
+        // the reservation is visible, and the previous tile's stores have
+        // finished reading the buffer the next copies go to
         __syncthreads();
-        const int64_t d = s_t;  // dispatch index
-        if (d >= total) break;
-
-        int c;
-        int64_t ti;
-        if (nrounds > 0) {
-            // interleaved: round r = the largest with rp[r] <= d, then the
-            // (d - rp[r])-th channel of the sorted order
-            int64_t lo = 0, hi = nrounds - 1;
-            while (lo < hi) {
-                const int64_t mid = (lo + hi + 1) >> 1;
-                if (__ldg(&p.rp[mid]) <= d) lo = mid; else hi = mid - 1;
-            }
-            ti = lo;
-            c = __ldg(&p.order[d - __ldg(&p.rp[lo])]);
-        } else {
-            // channel by channel: the largest c with tb[c] <= d
-            int lo = 0, hi = p.C - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(&p.tb[mid]) <= d) lo = mid; else hi = mid - 1;
-            }
-            c = lo;
-            ti = d - __ldg(&p.tb[c]);
+        const int64_t dn = s_t;
+        TileGeom gn{};
+        if (dn < total) {
+            gn = tile_geom<KT::kTile>(p, dn, nrounds);
+            issue_tile_load<N, W>(gn, s_tile4 + (cur ^ 1) * KT::kGran, tid);
         }
+        cp_async_commit();
+        cp_async_wait1();  // this thread's copies of the current tile
+
+        const int c = gc.c;
+        const int64_t ti = gc.ti, t = gc.t, nt = gc.nt, start = gc.start;
+        const int r = gc.r, skip = gc.skip;
+        const bool carry = gc.carry;
         const ChanInfo ci = p.chan[c];
-        const int64_t t = ci.slot + ti;  // the tile's look-back slot
-        const int64_t nt = ci.ntiles;
-        // Tiles of a channel with memory horizon P >= 0 overlap by P samples:
-        // tile 0 covers [0, T) from zi, tile ti > 0 computes
-        // [T + (ti - 1)(T - P) - P, ...) from zero state and stores all but
-        // its first P samples.  Other channels' tiles abut and carry the state.
-        const bool carry = ci.horizon < 0;
-        const int skip = (!carry && ti > 0) ? ci.horizon : 0;
-        const int64_t start =
-            skip ? KT::kTile + (ti - 1) * (KT::kTile - skip) - skip : ti * KT::kTile;
-        const int64_t rem = ci.len - start;
-        const int r = (int)(rem < KT::kTile ? rem : KT::kTile);  // valid samples
-        const float* src = p.x + ci.off + start;
+        float4* buf4 = s_tile4 + cur * KT::kGran;
+        float* buf = reinterpret_cast<float*>(buf4);
 
         if (c != cur_c) {  // CTA-uniform
             constexpr int n32 = sizeof(Coef32) / sizeof(float4), ndf = sizeof(CoefDF) / sizeof(float4);
@@ -432,19 +454,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
                 reinterpret_cast<float4*>(s_cdf)[i] = __ldg(gdf + i);
             cur_c = c;
         }
-
-        // S2: global -> shared (swizzled), zero beyond the channel end; all
-        // W + 1 warps take part
-        const bool vec = ((reinterpret_cast<uintptr_t>(src) & 15u) == 0) && r == KT::kTile;
-        if (vec) {
-            const float4* s4 = reinterpret_cast<const float4*>(src);
-#pragma unroll 4
-            for (int g = tid; g < KT::kGran; g += KT::kThreads) s_tile4[S::g(g)] = __ldcs(s4 + g);
-        } else {
-            for (int j = tid; j < KT::kTile; j += KT::kThreads)
-                s_tile[S::e(j)] = j < r ? __ldcs(src + j) : 0.0f;
-        }
-        __syncthreads();
+        __syncthreads();  // every thread's copies and the coefficients are in place
 
         if (coord) {
             if (carry)
@@ -455,7 +465,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             const int chunk = (W - warp) * 32 + lane;  // group W - warp of the tile
 #pragma unroll
             for (int g = 0; g < N / 4; ++g) {
-                const float4 q = s_tile4[S::g(chunk * (N / 4) + g)];
+                const float4 q = buf4[S::g(chunk * (N / 4) + g)];
                 v[4 * g + 0] = q.x;
                 v[4 * g + 1] = q.y;
                 v[4 * g + 2] = q.z;
@@ -468,7 +478,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             const int mq = q % N;
             // the owner's scratch: its own chunk of the tile buffer, unused
             // while the sections run (plain layout, only that lane touches it)
-            float* s_own = s_tile + chunk * N;
+            float* s_own = buf + chunk * N;
             if (ci.mode) {
                 if (carry) {
                     for (int k = 0; k < ci.K; ++k)
@@ -501,7 +511,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             __syncwarp();  // order the zf owner's scratch writes before the lanes' stores
 #pragma unroll
             for (int g = 0; g < N / 4; ++g)
-                s_tile4[S::g(chunk * (N / 4) + g)] =
+                buf4[S::g(chunk * (N / 4) + g)] =
                     make_float4(v[4 * g + 0], v[4 * g + 1], v[4 * g + 2], v[4 * g + 3]);
         }
         __syncthreads();
@@ -512,12 +522,15 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
             float4* d4 = reinterpret_cast<float4*>(dst);
 #pragma unroll 4
             for (int g = (skip >> 2) + tid; g < KT::kGran; g += KT::kThreads)
-                __stcs(d4 + g, s_tile4[S::g(g)]);
+                __stcs(d4 + g, buf4[S::g(g)]);
         } else {
-            for (int j = skip + tid; j < r; j += KT::kThreads) __stcs(dst + j, s_tile[S::e(j)]);
+            for (int j = skip + tid; j < r; j += KT::kThreads) __stcs(dst + j, buf[S::e(j)]);
         }
-        __syncthreads();
+        d = dn;
+        gc = gn;
+        cur ^= 1;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
 
     // The last CTA to finish opens a new look-back epoch and rewinds the tile
     // counter for the next launch on this workspace (every other CTA has

@@ -74,25 +74,29 @@ __device__ __forceinline__ float cabs_(cpx a) { return hypotf(a.re, a.im); }
 // are closer than 1e-4 (relative), where the partial fractions are not
 // reliable.
 __device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int lane, cpx* s_pole) {
-    // ||h||_2 lower bound: lane 0 filters a unit impulse for 64 samples
+    // ||h||_2 lower bound: lane 0 filters a unit impulse for 32 samples
     float e2 = 0.f;
     if (lane == 0) {
-        float z1[kMaxSections], z2[kMaxSections];
+        float cb0[kMaxSections], cb1[kMaxSections], cb2[kMaxSections], ca1[kMaxSections],
+            ca2[kMaxSections], z1[kMaxSections], z2[kMaxSections];
 #pragma unroll
-        for (int k = 0; k < kMaxSections; ++k) z1[k] = z2[k] = 0.f;
-        for (int n = 0; n < 64; ++n) {
+        for (int k = 0; k < kMaxSections; ++k) {
+            const bool on = k < K;
+            cb0[k] = on ? (float)rows[k][0] : 1.f;
+            cb1[k] = on ? (float)rows[k][1] : 0.f;
+            cb2[k] = on ? (float)rows[k][2] : 0.f;
+            ca1[k] = on ? (float)rows[k][3] : 0.f;
+            ca2[k] = on ? (float)rows[k][4] : 0.f;
+            z1[k] = z2[k] = 0.f;
+        }
+        for (int n = 0; n < 32; ++n) {
             float u = n == 0 ? 1.f : 0.f;
 #pragma unroll
             for (int k = 0; k < kMaxSections; ++k) {
-                if (k < K) {
-                    const float b0 = (float)rows[k][0], b1 = (float)rows[k][1],
-                                b2 = (float)rows[k][2], a1 = (float)rows[k][3],
-                                a2 = (float)rows[k][4];
-                    const float y = fmaf(b0, u, z1[k]);
-                    z1[k] = fmaf(b1, u, fmaf(-a1, y, z2[k]));
-                    z2[k] = fmaf(b2, u, -a2 * y);
-                    u = y;
-                }
+                const float y = fmaf(cb0[k], u, z1[k]);
+                z1[k] = fmaf(cb1[k], u, fmaf(-ca1[k], y, z2[k]));
+                z2[k] = fmaf(cb2[k], u, -ca2[k] * y);
+                u = y;
             }
             e2 = fmaf(u, u, e2);
         }
@@ -105,8 +109,8 @@ __device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int la
         const double disc = a1 * a1 - 4.0 * a2;
         cpx z;
         if (disc < 0.0) {
-            const double im = 0.5 * sqrt(-disc);
-            z = cpx{(float)(-0.5 * a1), (float)((lane & 1) ? -im : im)};
+            const float im = 0.5f * sqrtf((float)(-disc));
+            z = cpx{(float)(-0.5 * a1), (lane & 1) ? -im : im};
         } else {
             const double sq = sqrt(disc);
             z = cpx{(float)(0.5 * ((lane & 1) ? -a1 - sq : -a1 + sq)), 0.f};
@@ -119,54 +123,46 @@ __device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int la
     const float budget = kHorizonEps * h2;
     if (lane < np && !bad) {
         const cpx pi = s_pole[lane];
-        const float r = cabs_(pi);
+        const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
+        const float r = sqrtf(r2);
         if (r > 1e-20f) {
             if (!(r < 1.f - 1e-7f)) bad = true;
-            const cpx inv = cdiv(cpx{1.f, 0.f}, pi);
+            const float ir2 = 1.f / r2;
+            const cpx inv{pi.re * ir2, -pi.im * ir2};
             const cpx inv2 = cmul(inv, inv);
-            // section numerators at p_i (z^-1 = 1 / p_i)
-            cpx Bk[kMaxSections];
-#pragma unroll
-            for (int m = 0; m < kMaxSections; ++m) {
-                Bk[m] = cpx{1.f, 0.f};
-                if (m < K) {
-                    const float b0 = (float)rows[m][0], b1 = (float)rows[m][1],
-                                b2 = (float)rows[m][2];
-                    Bk[m] = cpx{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)),
-                                fmaf(b2, inv2.im, b1 * inv.im)};
-                }
-            }
             // walk the sections from the last to the first: den = prod over
             // the poles of sections >= k (except p_i) of (1 - p_l / p_i),
-            // num = prod_{m > k} B_m(p_i)
+            // num = prod_{m > k} B_m(p_i), B_m(z) = b0 + b1 z^-1 + b2 z^-2
             cpx num{1.f, 0.f}, den{1.f, 0.f};
-            float rz = 0.f;
+            float rz2 = 0.f;
             const int own = lane >> 1;
             for (int k = K - 1; k >= 0; --k) {
 #pragma unroll
                 for (int q = 0; q < 2; ++q) {
                     const int l = 2 * k + q;
                     if (l != lane) {
-                        const cpx f = cdiv(s_pole[l], pi);
+                        const cpx f = cmul(s_pole[l], inv);
                         const cpx g = cpx{1.f - f.re, -f.im};
-                        if (cabs_(g) < 1e-4f) bad = true;
+                        if (fmaf(g.re, g.re, g.im * g.im) < 1e-8f) bad = true;
                         den = cmul(den, g);
                     }
                 }
                 if (k <= own) {
-                    // state (k, 0) and (k, 1): residue num / den, times 1 / p_i for j = 1
-                    const float a = cabs_(num) / cabs_(den);
-                    rz = fmaxf(rz, a * fmaxf(1.f, 1.f / r));
+                    // states (k, 0) and (k, 1): |residue|^2 = |num|^2 / |den|^2
+                    // (times |1 / p_i|^2 for j = 1)
+                    const float a = fmaf(num.re, num.re, num.im * num.im) /
+                                    fmaf(den.re, den.re, den.im * den.im);
+                    rz2 = fmaxf(rz2, a * fmaxf(1.f, ir2));
                 }
-                num = cmul(num, Bk[k]);
+                const float b0 = (float)rows[k][0], b1 = (float)rows[k][1], b2 = (float)rows[k][2];
+                const cpx Bk{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
+                num = cmul(num, Bk);
             }
             // full cascade: num = prod_m B_m(p_i), den over all other poles
-            const float R = cabs_(num) / cabs_(den);
-            if (R > 0.f) {
-                const float n = logf(budget * (1.f - r) / ((float)np * R)) / logf(r);
-                ptail = fmaxf(ptail, n);
-            }
-            zsum = rz * powf(r, (float)T) / (1.f - r);
+            const float R = sqrtf(fmaf(num.re, num.re, num.im * num.im) /
+                                  fmaf(den.re, den.re, den.im * den.im));
+            if (R > 0.f) ptail = logf(budget * (1.f - r) / ((float)np * R)) / logf(r);
+            zsum = sqrtf(rz2) * powf(r, (float)T) / (1.f - r);
             if (!(ptail < 1e9f) || !(zsum < 1e30f)) bad = true;
         }
     }
@@ -253,29 +249,31 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
     }
 
     // ---- coefficient tables of channel c ----
+    // Warps 0..K-1: section k's row, then (lane 0) the squaring chain of its
+    // transition powers and (all lanes) the per-lane tables.  Warp 0 also
+    // decides the b0 factoring.  Warp kMaxSections: the memory horizon.  The
+    // cross-tile tables (powers of Theta) are only built for channels whose
+    // state is carried by the look-back, once the horizon warp has decided.
     const int c = blockIdx.x;
-    __shared__ double s_b0[kMaxSections];
-    __shared__ int s_mode;
-    __shared__ double s_G[kMaxSections];
     __shared__ double s_row[kMaxSections][5];
+    __shared__ double s_G[kMaxSections];
+    __shared__ int s_mode, s_horizon, s_err;
     __shared__ cpx s_pole[2 * kMaxSections];
     // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
     __shared__ dfm2 s_chain[kMaxSections][20];
 
-    if (tid == 0) p.chan[c].err = 0;
-    __syncthreads();
     const int K = p.K[c];
-    const bool valid_K = (K >= 0 && K <= kmax);
-    const int Kc = valid_K ? K : 0;
+    const int Kc = (K >= 0 && K <= kmax) ? K : 0;
     const int k = warp;
+    const bool active = k < Kc;
+    if (tid == 0) s_err = 0;
+    __syncthreads();
     double row[6] = {0, 0, 0, 1, 0, 0};
-    bool active = k < Kc;
     if (active) {
         const double* r = p.sos + ((int64_t)c * kmax + k) * 6;
         for (int i = 0; i < 6; ++i) row[i] = r[i];
-        bool ok = finite_row(row) && row[3] != 0.0;
-        if (!ok) {
-            if (lane == 0) atomicCAS(&p.chan[c].err, 0, (int)SOS_ERR_COEF);
+        if (!(finite_row(row) && row[3] != 0.0)) {
+            if (lane == 0) atomicCAS(&s_err, 0, (int)SOS_ERR_COEF);
             row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
         }
     }
@@ -293,50 +291,55 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         // both roots of z^2 + a1 z + a2 strictly inside the unit circle
         // (Jury: |a2| < 1 and |a1| < 1 + a2)
         if (!(fabs(a2) < 1.0 && fabs(a1) < 1.0 + a2) && lane == 0)
-            atomicCAS(&p.chan[c].err, 0, (int)SOS_ERR_UNSTABLE);
+            atomicCAS(&s_err, 0, (int)SOS_ERR_UNSTABLE);
     }
-    if (lane == 0 && k < kMaxSections) s_b0[k] = b0;
-    __syncthreads();
-    if (tid == 0) {
-        // factor b0 out of every section when that keeps the scaled signal in
-        // a safe FP32 range: every b0 nonzero and 2^-60 < |G_k| < 2^60
-        int mode = Kc > 0 ? 1 : 0;
-        double G = 1.0;
-        for (int j = 0; j < Kc; ++j) {
-            G *= s_b0[j];
-            if (!(s_b0[j] != 0.0) || !(fabs(G) > 0x1p-60) || !(fabs(G) < 0x1p60)) mode = 0;
-        }
-        G = 1.0;
-        for (int j = 0; j < kMaxSections; ++j) {
-            if (j < Kc && mode) G *= s_b0[j];
-            s_G[j] = mode ? G : 1.0;
-        }
-        s_mode = mode;
-        p.chan[c].mode = mode;
-    }
-    __syncthreads();
-    const int mode = s_mode;
+    __syncthreads();  // rows and errors in shared memory; nothing block-wide after this
 
     if (warp == kMaxSections) {
-        // the horizon warp: memory horizon and tile count of channel c
+        // the horizon warp: memory horizon of channel c (against the
+        // pipeline's segment length) and its work units: pipeline segments
+        // when it has a horizon, look-back tiles otherwise
         const int64_t T = (int64_t)p.W * kLanes * p.N;
-        const int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY) ? -1
-                                                           : channel_horizon(s_row, Kc, T, lane, s_pole);
+        const int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY)
+                          ? -1
+                          : channel_horizon(s_row, Kc, p.seg, lane, s_pole);
         if (lane == 0) {
             int64_t len = p.lengths[c];
             if (len < 0) len = 0;
             int64_t nt;
             if (len == 0) nt = 0;
-            else if (P >= 0 && len > T) nt = 1 + (len - T + (T - P) - 1) / (T - P);
+            else if (P >= 0) nt = (len + p.seg - 1) / p.seg;
             else nt = (len + T - 1) / T;
             p.chan[c].horizon = P;
             p.chan[c].ntiles = (int32_t)nt;
+            s_horizon = P;
         }
+        // release the section warps waiting for the decision (barrier 2:
+        // the Kc section warps and this one)
+        if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
         return;
+    }
+    if (warp == 0) {
+        // b0 factoring: every b0 nonzero and 2^-60 < |G_k| < 2^60 for the
+        // cumulative gains G_k = b0_1 ... b0_k (warp prefix product)
+        const double bj = lane < Kc ? s_row[lane < kMaxSections ? lane : 0][0] : 1.0;
+        double g = bj;
+        for (int d = 1; d < kMaxSections; d <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, g, d);
+            if (lane >= d) g *= t;
+        }
+        const bool ok = lane >= Kc || (bj != 0.0 && fabs(g) > 0x1p-60 && fabs(g) < 0x1p60);
+        const int mode = (Kc > 0 && __all_sync(0xffffffffu, ok)) ? 1 : 0;
+        if (lane < kMaxSections) s_G[lane] = mode ? g : 1.0;
+        if (lane == 0) {
+            s_mode = mode;
+            p.chan[c].mode = mode;
+            p.chan[c].err = s_err;
+        }
     }
     if (!active) return;
 
-    // ---- double-float squaring chain (lane 0) ----
+    // ---- Phi and Psi: double-float squaring chain (lane 0) ----
     const int N = p.N, W = p.W;
     if (lane == 0) {
         const dfm2 A{df_of_double(-a1), df{1.f, 0.f}, df_of_double(-a2), df{0.f, 0.f}};
@@ -346,37 +349,20 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         for (int j = 1; j < 5; ++j) s_chain[k][j] = dfm_mul(s_chain[k][j - 1], s_chain[k][j - 1]);
         s_chain[k][5] = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
         for (int r = 1; r < 5; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
-        dfm2 Th = dfm_identity();  // Theta = Psi^W, any W <= 31
-        for (int r = 0; r < 5; ++r)
-            if ((W >> r) & 1) Th = dfm_mul(Th, s_chain[k][5 + r]);
-        s_chain[k][10] = Th;
-        for (int i = 1; i < 10; ++i) s_chain[k][10 + i] = dfm_mul(s_chain[k][9 + i], s_chain[k][9 + i]);
     }
-    __syncwarp();
+    // barrier 1 (the Kc section warps): warp 0's mode and gains are in
+    // shared memory, and this warp's lane 0 has finished its chain
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * Kc) : "memory");
+    const int mode = s_mode;
 
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
     CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
     {
-        // Phi^lane, Theta^lane and Theta^(32 lane) by binary powering
-        dfm2 P = dfm_identity(), Q = dfm_identity(), R = dfm_identity();
+        // Phi^lane by binary powering
+        dfm2 P = dfm_identity();
         for (int j = 0; j < 5; ++j)
-            if ((lane >> j) & 1) {
-                P = dfm_mul(P, s_chain[k][j]);
-                Q = dfm_mul(Q, s_chain[k][10 + j]);
-                R = dfm_mul(R, s_chain[k][15 + j]);
-            }
+            if ((lane >> j) & 1) P = dfm_mul(P, s_chain[k][j]);
         out32->lane_pow[lane] = to_f4(P);
-        outdf->theta_pow[lane][0] = make_float4(Q.a.hi, Q.a.lo, Q.b.hi, Q.b.lo);
-        outdf->theta_pow[lane][1] = make_float4(Q.c.hi, Q.c.lo, Q.d.hi, Q.d.lo);
-        if (lane < 18) {
-            outdf->theta_hi[lane][0] = make_float4(R.a.hi, R.a.lo, R.b.hi, R.b.lo);
-            outdf->theta_hi[lane][1] = make_float4(R.c.hi, R.c.lo, R.d.hi, R.d.lo);
-        }
-        if (lane == 0) {
-            const dfm2 T32 = s_chain[k][15];
-            outdf->theta_pow[32][0] = make_float4(T32.a.hi, T32.a.lo, T32.b.hi, T32.b.lo);
-            outdf->theta_pow[32][1] = make_float4(T32.c.hi, T32.c.lo, T32.d.hi, T32.d.lo);
-        }
     }
     if (lane < 16) {
         dfm2 P = dfm_identity();
@@ -391,6 +377,38 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
         const double G = s_G[k];
         out32->misc = make_float4((float)b0, (float)G, (float)(1.0 / G), 0.0f);
+    }
+
+    // ---- Theta = A^T, only for channels carried by the look-back ----
+    asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
+    if (s_horizon >= 0) return;
+    if (lane == 0) {
+        dfm2 Th = dfm_identity();  // Theta = Psi^W, any W <= 31
+        for (int r = 0; r < 5; ++r)
+            if ((W >> r) & 1) Th = dfm_mul(Th, s_chain[k][5 + r]);
+        s_chain[k][10] = Th;
+        for (int i = 1; i < 10; ++i) s_chain[k][10 + i] = dfm_mul(s_chain[k][9 + i], s_chain[k][9 + i]);
+    }
+    __syncwarp();
+    {
+        // Theta^lane and Theta^(32 lane) by binary powering
+        dfm2 Q = dfm_identity(), R = dfm_identity();
+        for (int j = 0; j < 5; ++j)
+            if ((lane >> j) & 1) {
+                Q = dfm_mul(Q, s_chain[k][10 + j]);
+                R = dfm_mul(R, s_chain[k][15 + j]);
+            }
+        outdf->theta_pow[lane][0] = make_float4(Q.a.hi, Q.a.lo, Q.b.hi, Q.b.lo);
+        outdf->theta_pow[lane][1] = make_float4(Q.c.hi, Q.c.lo, Q.d.hi, Q.d.lo);
+        if (lane < 18) {
+            outdf->theta_hi[lane][0] = make_float4(R.a.hi, R.a.lo, R.b.hi, R.b.lo);
+            outdf->theta_hi[lane][1] = make_float4(R.c.hi, R.c.lo, R.d.hi, R.d.lo);
+        }
+        if (lane == 0) {
+            const dfm2 T32 = s_chain[k][15];
+            outdf->theta_pow[32][0] = make_float4(T32.a.hi, T32.a.lo, T32.b.hi, T32.b.lo);
+            outdf->theta_pow[32][1] = make_float4(T32.c.hi, T32.c.lo, T32.d.hi, T32.d.lo);
+        }
     }
 }
 
@@ -411,38 +429,67 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ int64_t s_carry;
     __shared__ int64_t s_wsum[32];
-    // ---- tile prefix ----
-    if (tid == 0) s_carry = 0;
+    // ---- prefixes: look-back tiles of the carried channels (tb) and
+    // pipeline segments of the others (tbp) ----
+    __shared__ int64_t s_carry2;
+    __shared__ int64_t s_wsum2[32];
+    if (tid == 0) {
+        s_carry = 0;
+        s_carry2 = 0;
+    }
     __syncthreads();
     int carried = 0;
     for (int base = 0; base < C; base += blockDim.x) {
         const int c = base + tid;
-        int64_t nt = 0;
+        int64_t nt = 0, ns = 0;
         if (c < C) {
             const ChanInfo ci = p.chan[c];
-            nt = ci.ntiles;
-            if (ci.horizon < 0 && nt > 1) carried = 1;
+            if (ci.horizon < 0) {
+                nt = ci.ntiles;
+                if (nt > 1) carried = 1;
+            } else {
+                ns = ci.ntiles;
+            }
         }
-        int64_t inc = nt;
+        int64_t inc = nt, inc2 = ns;
         for (int d = 1; d < 32; d <<= 1) {
             const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-            if (lane >= d) inc += o;
+            const int64_t o2 = __shfl_up_sync(0xffffffffu, inc2, d);
+            if (lane >= d) {
+                inc += o;
+                inc2 += o2;
+            }
         }
-        if (lane == 31) s_wsum[warp] = inc;
+        if (lane == 31) {
+            s_wsum[warp] = inc;
+            s_wsum2[warp] = inc2;
+        }
         __syncthreads();
-        int64_t wpre = 0;
-        for (int w = 0; w < warp; ++w) wpre += s_wsum[w];
-        const int64_t carry = s_carry;
-        if (c < C) p.tb[c] = carry + wpre + inc - nt;
+        int64_t wpre = 0, wpre2 = 0;
+        for (int w = 0; w < warp; ++w) {
+            wpre += s_wsum[w];
+            wpre2 += s_wsum2[w];
+        }
+        const int64_t carry = s_carry, carry2 = s_carry2;
+        if (c < C) {
+            p.tb[c] = carry + wpre + inc - nt;
+            p.tbp[c] = carry2 + wpre2 + inc2 - ns;
+        }
         __syncthreads();
-        if (tid == blockDim.x - 1) s_carry = carry + wpre + inc;
+        if (tid == blockDim.x - 1) {
+            s_carry = carry + wpre + inc;
+            s_carry2 = carry2 + wpre2 + inc2;
+        }
         __syncthreads();
     }
-    const int64_t total = s_carry;
+    const int64_t total = s_carry, total2 = s_carry2;
     const bool interleave = __syncthreads_or(carried) != 0 && C <= kMaxSortChannels;
     if (tid == 0) {
+        const bool bad = p.hdr->status == SOS_ERR_WORKSPACE;
         p.tb[C] = total;
-        p.hdr->total_tiles = p.hdr->status == SOS_ERR_WORKSPACE ? 0 : total;
+        p.tbp[C] = total2;
+        p.hdr->total_tiles = bad ? 0 : total;
+        p.hdr->total_pipe = bad ? 0 : total2;
         if (!interleave) p.hdr->nrounds = 0;
     }
     if (!interleave) return;
@@ -452,7 +499,8 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     for (int i = tid; i < n; i += blockDim.x) {
         // ascending sort of (MAX - ntiles, channel): decreasing tile count,
         // then increasing channel index; padding sorts last
-        const unsigned long long nt = i < C ? (unsigned long long)p.chan[i].ntiles : 0ull;
+        const unsigned long long nt =
+            (i < C && p.chan[i].horizon < 0) ? (unsigned long long)p.chan[i].ntiles : 0ull;
         s_key[i] = i < C ? (((0xffffffffull - nt) << 32) | (unsigned)i) : ~0ull;
     }
     __syncthreads();

@@ -39,7 +39,8 @@ struct WsHeader {
     int32_t nchan;          // channels of the latest call
     uint32_t done;          // CTAs of the running filter launch that have finished
     int64_t nrounds;        // interleaved dispatch: rounds (longest channel's tiles); 0 = channel-major
-    int64_t pad1[3];
+    int64_t total_pipe;     // segments of the section pipeline (channels within their horizon)
+    int64_t pad1[2];
 };
 static_assert(sizeof(WsHeader) == 64, "header size");
 
@@ -101,7 +102,7 @@ struct __align__(16) CoefDF {
 constexpr int kWords = 6;  // inc z1.hi, z1.lo, z2.hi, z2.lo, agg z1, z2
 
 struct WsLayout {
-    size_t hdr, chan, tb, order, rp, c32, cdf, slots, total;
+    size_t hdr, chan, tb, tbp, order, rp, c32, cdf, slots, total;
     int64_t cap_tiles;
 };
 
@@ -113,6 +114,7 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.hdr = o;   o = align_up(o + sizeof(WsHeader), 256);
     L.chan = o;  o = align_up(o + sizeof(ChanInfo) * (size_t)C, 256);
     L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
+    L.tbp = o;   o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
     L.order = o; o = align_up(o + sizeof(int32_t) * (size_t)C, 256);
     // rounds of the interleaved dispatch: at most the longest channel's tile
     // count, which overlapping tiles (stride >= T / 2) at most double
@@ -137,7 +139,8 @@ struct Params {
     float* zf;
     WsHeader* hdr;
     ChanInfo* chan;
-    int64_t* tb;         // tile prefix [C + 1]
+    int64_t* tb;         // look-back tile prefix over the carried channels [C + 1]
+    int64_t* tbp;        // segment prefix over the pipelined channels [C + 1]
     int32_t* order;      // channels by decreasing tile count (interleaved dispatch)
     int64_t* rp;         // tiles dispatched before round r [nrounds + 1]
     Coef32* c32;
@@ -150,6 +153,7 @@ struct Params {
     int32_t W;           // warps per tile
     int32_t flags_opt;   // SOS_FLAG_*
     int32_t pad;
+    int64_t seg;         // pipeline segment length (samples, a multiple of 32 N)
 };
 
 // ---------------------------------------------------------------------------

@@ -265,13 +265,12 @@ def test_horizons_bound_the_true_impulse_tail():
         if hz[c] < 0:
             assert tiles[c] == -(-L // T)
             continue
-        assert hz[c] % 16 == 0 and 2 * int(K[c]) <= hz[c] <= T // 2
-        assert tiles[c] == 1 + -(-(L - T) // (T - hz[c]))
+        # pipelined channel: segments of at most 64 groups, warm-up <= half
+        assert hz[c] % 16 == 0 and 2 * int(K[c]) <= hz[c] <= 32 * 1024
+        assert 1 <= tiles[c] <= -(-L // (8 * 1024))
         h = _impulse_response(sos[c, :K[c]], 1 << 17)
         tail = np.abs(h[hz[c]:]).sum()
         assert tail <= 2.0 ** -30 * np.sqrt((h ** 2).sum()), (c, hz[c], tail)
-    # at T = 8192 a few of the slowest-decaying random cascades (radius up to
-    # 0.995) need more than T / 2 and are carried instead
     assert (hz[:64] >= 0).mean() >= 0.85, hz[:64]
 
 
