@@ -180,6 +180,35 @@ sos_status sos_filter_static(const float *x, const double *sos, const int32_t *K
  * of the most recent call that used this workspace. */
 sos_status sos_device_status(void *workspace, void *stream);
 
+/* Bytes of device workspace for sos_filter_backward with these sizes (the
+ * forward workspace plus kmax * sum(lengths) floats for the section outputs
+ * and 5 doubles per section for the coefficient sums).  0 if invalid. */
+size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64_t *lengths_host,
+                                   const sos_tuning *tuning);
+
+/* Gradients of a loss L through sos_filter (reverse mode, the transpose of
+ * the banded-Toeplitz system of Eq. recursive_equation_block_form): given
+ * grad_y = dL/dy (device, packed like y) and grad_zf = dL/dzf ([C][kmax][2],
+ * may be NULL = zero), writes grad_x = dL/dx (packed like x), grad_sos =
+ * dL/d(sos) ([C][kmax][6] float64, w.r.t. the rows as given, a0 included;
+ * zero rows past K[c]) and grad_zi = dL/dzi ([C][kmax][2], may be NULL).
+ * x, sos, K, lengths, zi are those of the forward call.
+ * Per section the adjoint state runs backwards in time with A^T, i.e. the
+ * time-reversed all-pole recursion lambda_n = g_n - a1 lambda_{n+1} -
+ * a2 lambda_{n+2} started from dL/dzf, then dL/du = b0 lambda_n +
+ * b1 lambda_{n+1} + b2 lambda_{n+2}; dL/db_j = sum lambda_{n+j} u_n,
+ * dL/da_j = -sum lambda_{n+j} y_n, dL/dzi = (lambda_0, lambda_1).  The
+ * section outputs are recomputed by a forward pass into the workspace.
+ * Channels without a memory horizon run as one segment each (correct, but
+ * without parallelism inside the channel).  Asynchronous on `stream`;
+ * argument errors are returned at once, device errors go to the status word. */
+sos_status sos_filter_backward(const float *x, const double *sos, const int32_t *K,
+                               int32_t n_channels, int32_t kmax, const int64_t *lengths,
+                               const int64_t *lengths_host, const float *zi, const float *grad_y,
+                               const float *grad_zf, float *grad_x, double *grad_sos,
+                               float *grad_zi, void *workspace, size_t ws_bytes,
+                               const sos_tuning *tuning, void *stream);
+
 /* Waits for `stream`, then copies from the channel table of the most recent
  * sos_prepare on this workspace, for channels [first, first + count): the
  * memory horizon P of each (>= 0: tiles overlap by P samples and start from

@@ -21,7 +21,8 @@ import torch
 from . import _abi
 from ._abi import SosError, sos_tuning  # noqa: F401
 
-__all__ = ["SosFilter", "sosfilt", "SosError", "sos_tuning", "build"]
+__all__ = ["SosFilter", "sosfilt", "sosfilt_diff", "SosFilterFunction", "SosError", "sos_tuning",
+           "build"]
 
 
 def build(force: bool = False) -> str:
@@ -126,6 +127,45 @@ class SosFilter:
             raise SosError(st, "sos_apply")
         return y, zf
 
+    def backward(self, x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor],
+                 zi: Optional[torch.Tensor], grad_y: torch.Tensor,
+                 grad_zf: Optional[torch.Tensor] = None, want_zi: bool = True):
+        """dL/dx, dL/dsos (float64, w.r.t. the rows as given) and dL/dzi from
+        dL/dy and dL/dzf, by the library's adjoint kernels."""
+        C, kmax = self.n_channels, self.kmax
+        sos = sos.reshape(C, kmax, 6).contiguous()
+        if K is None:
+            K = torch.full((C,), kmax, dtype=torch.int32, device=x.device)
+        if not hasattr(self, "_bws"):
+            nb = _abi.sos_backward_workspace_size(C, kmax, self.lengths_host.data_ptr(),
+                                                  self.tuning)
+            if nb == 0:
+                raise ValueError("unsupported sizes for the backward pass")
+            self._bws_bytes = nb
+            self._bws = torch.zeros(nb, dtype=torch.uint8, device=self.device)
+        grad_y = grad_y.contiguous()
+        if grad_y.dtype != torch.float32 or grad_y.numel() != self.total:
+            raise ValueError("grad_y must be float32 with sum(lengths) elements")
+        gx = torch.empty_like(grad_y)
+        gsos = torch.empty((C, kmax, 6), dtype=torch.float64, device=x.device)
+        gzi = torch.empty((C, kmax, 2), dtype=torch.float32, device=x.device) if want_zi else None
+        gzf = grad_zf.reshape(C, kmax, 2).contiguous() if grad_zf is not None else None
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_filter_backward(x.data_ptr(), sos.data_ptr(), K.data_ptr(), C, kmax,
+                                      self.lengths.data_ptr(), self.lengths_host.data_ptr(),
+                                      zi.data_ptr() if zi is not None else 0, grad_y.data_ptr(),
+                                      gzf.data_ptr() if gzf is not None else 0, gx.data_ptr(),
+                                      gsos.data_ptr(), gzi.data_ptr() if gzi is not None else 0,
+                                      self._bws.data_ptr(), self._bws_bytes, self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_filter_backward")
+        return gx, gsos, gzi
+
+    def backward_status(self) -> int:
+        """Device-side status of the latest backward call (synchronises)."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        return _abi.sos_device_status(self._bws.data_ptr(), stream)
+
     def plan_info(self):
         """(horizon, tiles) per channel from the latest prepare: int32 host
         tensors; horizon -1 marks channels whose state is carried by the
@@ -175,3 +215,54 @@ def sosfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None
         if st != 0:
             raise SosError(st, "sos_filter (device)")
     return y, zf
+
+
+class SosFilterFunction(torch.autograd.Function):
+    """y, zf = sosfilt(x, sos, zi) with gradients for x, sos and zi from the
+    library's adjoint kernels (``SosFilter.backward``)."""
+
+    @staticmethod
+    def forward(ctx, x, sos, zi, plan, K):
+        y, zf = plan(x.contiguous(), sos.contiguous(), K,
+                     zi.contiguous() if zi is not None else None)
+        ctx.plan = plan
+        ctx.K = K
+        ctx.save_for_backward(x, sos, zi if zi is not None else torch.empty(0))
+        ctx.has_zi = zi is not None
+        return y, zf
+
+    @staticmethod
+    def backward(ctx, grad_y, grad_zf):
+        x, sos, zi = ctx.saved_tensors
+        zi = zi if ctx.has_zi else None
+        if grad_y is None:
+            grad_y = torch.zeros_like(x)
+        gx, gsos, gzi = ctx.plan.backward(x, sos, ctx.K, zi, grad_y, grad_zf,
+                                          want_zi=ctx.has_zi)
+        return gx, gsos.reshape(sos.shape), (gzi.reshape(zi.shape) if ctx.has_zi else None), \
+            None, None
+
+
+def sosfilt_diff(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                 lengths=None, zi: Optional[torch.Tensor] = None, tuning=None):
+    """Differentiable ``sosfilt``: (y, zf) with autograd through x, sos and zi."""
+    _check_device(x, "x")
+    sos3 = sos if sos.dim() == 3 else sos.unsqueeze(0)
+    C, kmax = int(sos3.shape[0]), int(sos3.shape[1])
+    if lengths is None:
+        if C != 1:
+            raise ValueError("lengths are required for more than one channel")
+        lengths = [x.numel()]
+    lh = tuple(int(v) for v in torch.as_tensor(lengths).reshape(-1).tolist())
+    key = (x.device, lh, kmax, tuple(tuning) if tuning is not None else None)
+    plan = _plans.get(key)
+    if plan is None:
+        plan = SosFilter(lh, kmax, tuning=tuning, device=x.device)
+        if len(_plans) > 16:
+            _plans.clear()
+        _plans[key] = plan
+    if K is None:
+        K = torch.full((C,), kmax, dtype=torch.int32, device=x.device)
+    if zi is not None:
+        zi = zi.reshape(C, kmax, 2)
+    return SosFilterFunction.apply(x, sos3, zi, plan, K)

@@ -78,6 +78,11 @@ def load(build_if_missing: bool = False):
         lib.sos_filter_static.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
+        lib.sos_backward_workspace_size.argtypes = [i32, i32, vp, tp]
+        lib.sos_backward_workspace_size.restype = sz
+        lib.sos_filter_backward.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, vp, vp,
+                                            vp, sz, tp, vp]
+        lib.sos_filter_backward.restype = ctypes.c_int
         lib.sos_plan_query.argtypes = [vp, i32, i32, vp, vp, vp]
         lib.sos_plan_query.restype = ctypes.c_int
         _lib = lib
@@ -138,6 +143,24 @@ def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y,
 
 def sos_device_status(ws_ptr: int, stream: int) -> int:
     return int(load().sos_device_status(ctypes.c_void_p(ws_ptr), ctypes.c_void_p(stream)))
+
+
+def sos_backward_workspace_size(n_channels: int, kmax: int, lengths_host_ptr: int,
+                                tuning=None) -> int:
+    return int(load().sos_backward_workspace_size(n_channels, kmax,
+                                                  ctypes.c_void_p(lengths_host_ptr),
+                                                  _tuning(tuning)))
+
+
+def sos_filter_backward(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, grad_y, grad_zf,
+                        grad_x, grad_sos, grad_zi, ws, ws_bytes, tuning, stream) -> int:
+    """All pointer arguments are integers (0 for NULL)."""
+    V = ctypes.c_void_p
+    return int(load().sos_filter_backward(V(x), V(sos), V(K), n_channels, kmax, V(lengths),
+                                          V(lengths_host), V(zi or None), V(grad_y),
+                                          V(grad_zf or None), V(grad_x), V(grad_sos),
+                                          V(grad_zi or None), V(ws), ws_bytes, _tuning(tuning),
+                                          V(stream)))
 
 
 def sos_plan_query(ws_ptr: int, first: int, count: int, horizon_ptr: int, tiles_ptr: int,

@@ -8,6 +8,7 @@ namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream);
 cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream);
 cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream);
+cudaError_t launch_adjoint(const Params& p, int64_t grid, double* grad_sos, cudaStream_t stream);
 bool forward_supported(int N, int W);
 bool pipe_supported(int N);
 }  // namespace sosf
@@ -152,6 +153,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->W = tu.W;
     p->flags_opt = tu.flags;
     p->seg = segment_length(total_len, tu.N);
+    p->total = total_len;
     *tiles_out = tiles;
     *total_len_out = total_len;
     return SOS_OK;
@@ -289,6 +291,86 @@ sos_status sos_plan_query(void* workspace, int32_t first, int32_t count, int32_t
             if (tiles) tiles[c0 + i] = buf[i].ntiles;
         }
     }
+    return SOS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// backward
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BwdLayout {
+    size_t inter, gacc, total;
+};
+
+BwdLayout bwd_layout(size_t base, int32_t C, int32_t kmax, int64_t total_len) {
+    BwdLayout L;
+    size_t o = align_up(base, 256);
+    L.inter = o;
+    o = align_up(o + sizeof(float) * (size_t)kmax * (size_t)total_len, 256);
+    L.gacc = o;
+    o = align_up(o + sizeof(double) * 5 * (size_t)C * (size_t)kmax, 256);
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64_t* lengths_host,
+                                   const sos_tuning* tuning) {
+    const size_t base = sos_workspace_size(n_channels, kmax, lengths_host, tuning);
+    if (base == 0) return 0;
+    int64_t total = 0;
+    for (int32_t c = 0; c < n_channels; ++c) total += lengths_host[c];
+    return bwd_layout(base, n_channels, kmax, total).total;
+}
+
+sos_status sos_filter_backward(const float* x, const double* sos, const int32_t* K,
+                               int32_t n_channels, int32_t kmax, const int64_t* lengths,
+                               const int64_t* lengths_host, const float* zi, const float* grad_y,
+                               const float* grad_zf, float* grad_x, double* grad_sos,
+                               float* grad_zi, void* workspace, size_t ws_bytes,
+                               const sos_tuning* tuning, void* stream) {
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    sos_status st = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p, &tiles,
+                          &total);
+    if (st != SOS_OK) return st;
+    if (!sos || !K || !lengths || !grad_sos) return SOS_ERR_ARG;
+    if (total > 0 && (!x || !grad_y || !grad_x)) return SOS_ERR_ARG;
+    const size_t base = ws_layout(n_channels, kmax, tiles).total;
+    const BwdLayout BL = bwd_layout(base, n_channels, kmax, total);
+    if (ws_bytes < BL.total) return SOS_ERR_WORKSPACE;
+    char* ws = static_cast<char*>(workspace);
+    cudaStream_t sm = static_cast<cudaStream_t>(stream);
+    p.sos = sos;
+    p.K = K;
+    p.lengths = lengths;
+    p.flags_opt |= kFlagBackwardPlan;
+    p.inter = reinterpret_cast<float*>(ws + BL.inter);
+    p.gacc = reinterpret_cast<double*>(ws + BL.gacc);
+    if (launch_plan(p, sm) != cudaSuccess) return SOS_ERR_CUDA;
+    const int64_t grid = (int64_t)(device_sms() > 0 ? device_sms() : 1) * kPipeCtasPerSm;
+    // forward pass keeping every section's output
+    p.x = x;
+    p.y = nullptr;
+    p.zi = zi;
+    p.zf = nullptr;
+    if (total > 0 && launch_pipe(p, grid, sm) != cudaSuccess) return SOS_ERR_CUDA;
+    if (cudaMemsetAsync(p.gacc, 0, sizeof(double) * 5 * (size_t)n_channels * kmax, sm) !=
+        cudaSuccess)
+        return SOS_ERR_CUDA;
+    // adjoint pass and the coefficient gradients
+    p.gy = grad_y;
+    p.gzf = grad_zf;
+    p.gx = grad_x;
+    p.gzi = grad_zi;
+    if (launch_adjoint(p, total > 0 ? grid : 0, grad_sos, sm) != cudaSuccess) return SOS_ERR_CUDA;
     return SOS_OK;
 }
 

@@ -300,17 +300,23 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         // pipeline's segment length) and its work units: pipeline segments
         // when it has a horizon, look-back tiles otherwise
         const int64_t T = (int64_t)p.W * kLanes * p.N;
-        const int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY)
-                          ? -1
-                          : channel_horizon(s_row, Kc, p.seg, lane, s_pole);
+        int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY)
+                    ? -1
+                    : channel_horizon(s_row, Kc, p.seg, lane, s_pole);
+        // backward plans have no look-back: a channel without a horizon is
+        // one segment, run from its start to its end by one pipeline
+        const int single = (P < 0 && (p.flags_opt & kFlagBackwardPlan)) ? 1 : 0;
+        if (single) P = 0;
         if (lane == 0) {
             int64_t len = p.lengths[c];
             if (len < 0) len = 0;
             int64_t nt;
             if (len == 0) nt = 0;
+            else if (single) nt = 1;
             else if (P >= 0) nt = (len + p.seg - 1) / p.seg;
             else nt = (len + T - 1) / T;
             p.chan[c].horizon = P;
+            p.chan[c].single = single;
             p.chan[c].ntiles = (int32_t)nt;
             s_horizon = P;
         }
@@ -377,6 +383,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
         const double G = s_G[k];
         out32->misc = make_float4((float)b0, (float)G, (float)(1.0 / G), 0.0f);
+        out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
     }
 
     // ---- Theta = A^T, only for channels carried by the look-back ----

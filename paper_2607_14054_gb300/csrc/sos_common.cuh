@@ -54,7 +54,7 @@ struct ChanInfo {
     int64_t slot;     // first look-back slot of the channel (ceil(len / T) slots)
     int32_t horizon;  // >= 0: memory horizon P (tiles overlap by P samples, no carry);
                       // -1: the state is carried by the look-back
-    int32_t pad;
+    int32_t single;   // 1: the whole channel is one pipeline segment (backward plans)
 };
 static_assert(sizeof(ChanInfo) == 48, "channel table entry");
 
@@ -68,6 +68,10 @@ static_assert(sizeof(ChanInfo) == 48, "channel table entry");
 // unit circle, coincident poles) keep the decoupled look-back.
 constexpr float kHorizonEps = 0x1p-30f;
 
+// Internal plan flag (above the public SOS_FLAG_* bits): the plan of a
+// backward call, where channels without a horizon become single segments.
+constexpr int32_t kFlagBackwardPlan = 1 << 16;
+
 // Per (channel, section) FP32 coefficients and transition-matrix powers.
 // The DF2T state transition of one sample is A = [[-a1, 1], [-a2, 0]];
 // Phi = A^N advances one lane chunk, Psi = A^{N L} one warp group.  All
@@ -76,6 +80,7 @@ constexpr float kHorizonEps = 0x1p-30f;
 struct __align__(16) Coef32 {
     float4 ab;            // a1, a2, b1, b2  (b1, b2 divided by b0 when factored)
     float4 misc;          // b0, G_k (cumulative gain), 1/G_k, unused
+    float4 braw;          // b0, b1, b2 normalised by a0 only (the adjoint's FIR)
     float4 phi_pow[5];    // Phi^(2^j), j = 0..4 (lane scan)
     float4 psi_pow[4];    // Psi^(2^r), r = 0..3 (warp scan)
     float4 psi_w[16];     // Psi^w, w = 0..15 (fold the tile state into warp w)
@@ -154,6 +159,13 @@ struct Params {
     int32_t flags_opt;   // SOS_FLAG_*
     int32_t pad;
     int64_t seg;         // pipeline segment length (samples, a multiple of 32 N)
+    float* inter;        // [kmax][total] section outputs (backward's forward pass), or null
+    const float* gy;     // backward: dL/dy [total]
+    const float* gzf;    // backward: dL/dzf [C][kmax][2], or null
+    float* gx;           // backward: dL/dx [total]
+    float* gzi;          // backward: dL/dzi [C][kmax][2], or null
+    double* gacc;        // backward: [C][kmax][5] sums for b0, b1, b2, a1, a2
+    int64_t total;       // samples of all channels
 };
 
 // ---------------------------------------------------------------------------
