@@ -69,7 +69,11 @@ typedef enum sos_status {
  *             16, 32 or 64 (0 = default 32).
  *   warps:    W, warps per tile (one tile = W*32*N samples): 4, 8 or 16
  *             (0 = default 8).
- *   algo:     recursive-stage solver: 0 = default, 1 = PH (Sec. VI-B).
+ *   algo:     recursive-stage solver: 0 = default (PH), 1 = PH (Sec. VI-B),
+ *             2 = cyclic reduction (Sec. VI-C) for every section whose
+ *             reduction is well conditioned (max |f_i / e_i| <= 100 over the
+ *             log2 N levels; the others keep PH).  CR applies to channels run
+ *             by the section pipeline; channels carried by the look-back use PH.
  *   flags:    bit 0 (SOS_FLAG_CHECK_STABLE): reject sections whose poles are
  *             not strictly inside the unit circle.
  *             bit 1 (SOS_FLAG_CARRY_ONLY): carry every channel's state between

@@ -31,7 +31,7 @@ bool resolve_tuning(const sos_tuning* t, Tune* out) {
         if (t->algo) r.algo = t->algo;
         r.flags = t->flags;
     }
-    if (r.algo != 1) return false;
+    if (r.algo != 1 && r.algo != 2) return false;
     if (!forward_supported(r.N, r.W) || !pipe_supported(r.N)) return false;
     *out = r;
     return true;
@@ -152,6 +152,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->N = tu.N;
     p->W = tu.W;
     p->flags_opt = tu.flags;
+    p->algo = tu.algo;
     p->seg = segment_length(total_len, tu.N);
     p->total = total_len;
     *tiles_out = tiles;

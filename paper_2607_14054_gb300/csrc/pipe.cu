@@ -30,7 +30,7 @@
 namespace sosf {
 
 // The groups of one segment through section k (warp 1 + k).
-template <int N, bool FACT>
+template <int N, bool FACT, bool CR>
 __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegGeom& sg, int k,
                                                      PipeShared& sh, float* ring, int& s,
                                                      unsigned& use, const float4 ab,
@@ -70,8 +70,12 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
             v[4 * j + 3] = t.w;
         }
         const bool zf_owner = g == g_last && lane == owner;
-        pipe_section<N, FACT>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
-                              FACT ? G : 1.f);
+        if (CR)
+            pipe_section_cr<N, FACT>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row, zf_dst,
+                                     FACT ? G : 1.f);
+        else
+            pipe_section<N, FACT>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
+                                  FACT ? G : 1.f);
         if (p.inter) {
             // the backward's forward pass: the true section output (times
             // G_k when b0 is factored), for the segment's own samples
@@ -201,13 +205,20 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
                     lp = __ldg(&cf->lane_pow[lane]);
                     __syncwarp();
                     if (lane < 5) sh.phi[k][lane] = __ldg(&cf->phi_pow[lane]);
+                    if (lane < 14) sh.cr[k][lane] = __ldg(&cf->cr_lv[0] + lane);
                     __syncwarp();
                     cur_c = sg.c;
                 }
-                if (p.chan[sg.c].mode)
-                    pipe_segment_section<N, true>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                const bool cr = p.algo == 2 && sh.cr[k][13].w != 0.f;
+                const bool fact = p.chan[sg.c].mode != 0;
+                if (fact && cr)
+                    pipe_segment_section<N, true, true>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                else if (fact)
+                    pipe_segment_section<N, true, false>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                else if (cr)
+                    pipe_segment_section<N, false, true>(p, sg, k, sh, ring, s, use, ab, misc, lp);
                 else
-                    pipe_segment_section<N, false>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                    pipe_segment_section<N, false, false>(p, sg, k, sh, ring, s, use, ab, misc, lp);
             } else {
                 // past the channel's K: pass the groups through
                 for (int g = 0; g < sg.ngroups; ++g) {

@@ -99,4 +99,137 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     __syncwarp();
 }
 
+// The same section solved by cyclic reduction (Sec. VI-C) instead of PH.
+// Register m across the 32 lanes is the strided block y_m of Eq.
+// cr_permuted_system, and S_R (the shift onto the previous lane) is a
+// one-lane shuffle, zero for lane 0: the group's incoming DF2T state enters
+// as the corrections to lane 0's v_0 and v_1 (Eq. feedforward_block_uniform).
+//   reduction (Eq. cr_elim_step2), level i, s = 2^i, kept blocks m = 2s-1,
+//     4s-1, ..: v_m <- v_m - e_i v_{m-s} + f_i v_{m-2s}, and the eliminated
+//     block keeps v~_{m-s} = v_{m-s} - g_i v_{m-2s} (g_i = f_i / e_i);
+//   terminal block (Eq. cr_terminal_block): Y_l + e_n Y_{l-1} + f_n Y_{l-2}
+//     = V_l across lanes, by a 5-round scan;
+//   back substitution (Eqs. cr_backsub_penultimate, cr_backsub_final):
+//     y_{m-s} = v~_{m-s} - c_i y_{m-2s} - d_i y_{m-4s}, indices below 0
+//     taken from the previous lane (S_R) or the one before (S_R^2).
+// Sequential depth log2 N per stage instead of N.
+template <int N, bool FACT>
+__device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, const float b0,
+                                                const float4* cr, float& Z1, float& Z2,
+                                                bool zf_owner, int mq, float* s_own,
+                                                float* zf_dst, float G) {
+    // cr: cr_lv[6], cr_d[2], cr_tpow[5], cr_misc (the Coef32 fields, staged)
+    const float4* lv = cr;
+    const float* dd = reinterpret_cast<const float*>(cr + 6);
+    const float4* tp = cr + 8;
+    const int lane = threadIdx.x & 31;
+    const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
+    const float zi1 = Z1, zi2 = Z2;
+
+    float xq = 0.f, xqm1 = 0.f;
+    __syncwarp();
+    if (zf_owner) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) s_own[m] = v[m];
+        xq = s_own[mq];
+        xqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
+    }
+
+    // S3 with the true history: the previous lane's last two inputs (lane 0's
+    // history is inside the group state)
+    const float xl1 = v[N - 1], xl2 = v[N - 2];
+    float px1 = __shfl_up_sync(0xffffffffu, xl1, 1);
+    float px2 = __shfl_up_sync(0xffffffffu, xl2, 1);
+    if (lane == 0) {
+        px1 = 0.f;
+        px2 = 0.f;
+    }
+#pragma unroll
+    for (int m = N - 1; m >= 2; --m)
+        v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
+    v[1] = fmaf(b2, px1, fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]));
+    v[0] = fmaf(b2, px2, fmaf(b1, px1, FACT ? v[0] : b0 * v[0]));
+    if (lane == 0) {
+        v[0] += zi1;
+        v[1] += zi2;
+    }
+
+    // reduction
+#pragma unroll
+    for (int i = 0; (1 << i) < N; ++i) {
+        const int s = 1 << i;
+        const float4 q = lv[i];  // e, f, g, c
+        float pv = __shfl_up_sync(0xffffffffu, v[N - 1], 1);
+        if (lane == 0) pv = 0.f;
+#pragma unroll
+        for (int m = N - 1; m >= 2 * s - 1; m -= 2 * s) {
+            const float vms = v[m - s];
+            const float vm2s = m - 2 * s >= 0 ? v[m - 2 * s] : pv;
+            v[m] = fmaf(q.y, vm2s, fmaf(-q.x, vms, v[m]));
+            v[m - s] = fmaf(-q.z, vm2s, vms);
+        }
+    }
+
+    // terminal recurrence across lanes: inclusive scan of (Y_l, Y_{l-1})
+    float S1 = v[N - 1], S2 = 0.f;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int d = 1 << j;
+        float t1 = __shfl_up_sync(0xffffffffu, S1, d);
+        float t2 = __shfl_up_sync(0xffffffffu, S2, d);
+        t1 = lane >= d ? t1 : 0.f;
+        t2 = lane >= d ? t2 : 0.f;
+        S1 = fmaf(tp[j].x, t1, fmaf(tp[j].y, t2, S1));
+        S2 = fmaf(tp[j].z, t1, fmaf(tp[j].w, t2, S2));
+    }
+    v[N - 1] = S1;
+    const float Y1 = S2;  // S_R y_{N-1}: the previous lane's (0 for lane 0)
+    float Y2 = __shfl_up_sync(0xffffffffu, S2, 1);  // S_R^2 y_{N-1}
+    if (lane == 0) Y2 = 0.f;
+
+    // back substitution
+    constexpr int kLv = N == 16 ? 4 : N == 32 ? 5 : 6;
+#pragma unroll
+    for (int ii = 0; ii < kLv; ++ii) {
+        const int lvl = kLv - 1 - ii;
+        const int s = 1 << lvl;
+        const float c = lv[lvl].w, d = dd[lvl];
+        float sh4 = Y2;  // S_R y_{N-2s-1}, or S_R^2 y_{N-1} when 2s = N
+        if (2 * s + 1 <= N) {
+            sh4 = __shfl_up_sync(0xffffffffu, v[(N - 2 * s - 1) >= 0 ? N - 2 * s - 1 : 0], 1);
+            if (lane == 0) sh4 = 0.f;
+        }
+#pragma unroll
+        for (int m = 2 * s - 1; m < N; m += 2 * s) {
+            const float ym2s = m - 2 * s >= 0 ? v[m - 2 * s >= 0 ? m - 2 * s : 0] : Y1;
+            const int q = m - 4 * s;
+            const float ym4s = q >= 0 ? v[q >= 0 ? q : 0] : (q == -1 ? Y1 : sh4);
+            v[m - s] = fmaf(-d, ym4s, fmaf(-c, ym2s, v[m - s]));
+        }
+    }
+
+    // the group's outgoing state, from lane 31's last two inputs and outputs
+    const float o1 = fmaf(b1, xl1, fmaf(b2, xl2, fmaf(-a1, v[N - 1], -a2 * v[N - 2])));
+    const float o2 = fmaf(b2, xl1, -a2 * v[N - 1]);
+    Z1 = __shfl_sync(0xffffffffu, o1, 31);
+    Z2 = __shfl_sync(0xffffffffu, o2, 31);
+
+    // S8: final state at the channel's last sample
+    if (zf_owner) {
+        // DF2T z2 entering this lane: b2 x_{-1} - a2 y_{-1}
+        const float zin2 = lane == 0 ? zi2 : fmaf(b2, px1, -a2 * Y1);
+#pragma unroll
+        for (int m = 0; m < N; ++m) s_own[m] = v[m];
+        const float yq = s_own[mq];
+        const float yqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
+        float f1;
+        if (mq >= 1) f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
+        else f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
+        const float f2 = fmaf(b2, xq, -a2 * yq);
+        zf_dst[0] = f1 * G;
+        zf_dst[1] = f2 * G;
+    }
+    __syncwarp();
+}
+
 }  // namespace sosf

@@ -356,6 +356,33 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         s_chain[k][5] = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
         for (int r = 1; r < 5; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
     }
+    // cyclic-reduction coefficients in FP64 (lane 1, alongside lane 0's chain)
+    if (lane == 1 && p.algo == 2) {
+        Coef32* o = p.c32 + ((int64_t)c * kmax + k);
+        double e = a1, f = a2, kappa = 0.0;
+        float dd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int lv = 0;
+        for (int n = 1; n < N; n <<= 1, ++lv) {
+            const double g = f / e;
+            if (e == 0.0 || !isfinite(g)) kappa = INFINITY;
+            else if (fabs(g) > kappa) kappa = fabs(g);
+            o->cr_lv[lv] = make_float4((float)e, (float)f, (float)g, (float)(e - g));
+            dd[lv] = (float)(-f * g);
+            const double e2 = 2.0 * f - e * e;
+            f = f * f;
+            e = e2;
+        }
+        o->cr_d[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+        o->cr_d[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
+        // terminal scan powers C^(2^j), C = [[-e_n, -f_n], [1, 0]], double-float
+        dfm2 C{df_of_double(-e), df_of_double(-f), df{1.f, 0.f}, df{0.f, 0.f}};
+        for (int j = 0; j < 5; ++j) {
+            o->cr_tpow[j] = to_f4(C);
+            C = dfm_mul(C, C);
+        }
+        const bool ok = kappa <= kCrKappaMax;
+        o->cr_misc = make_float4((float)e, (float)f, (float)kappa, ok ? 1.f : 0.f);
+    }
     // barrier 1 (the Kc section warps): warp 0's mode and gains are in
     // shared memory, and this warp's lane 0 has finished its chain
     asm volatile("bar.sync 1, %0;" ::"r"(32 * Kc) : "memory");

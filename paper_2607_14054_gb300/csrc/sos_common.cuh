@@ -68,6 +68,11 @@ static_assert(sizeof(ChanInfo) == 48, "channel table entry");
 // unit circle, coincident poles) keep the decoupled look-back.
 constexpr float kHorizonEps = 0x1p-30f;
 
+// Cyclic reduction divides by e_i at every level (c_i = e_i - f_i / e_i);
+// a section whose |f_i / e_i| exceeds this at some level keeps PH, which
+// divides by nothing.
+constexpr double kCrKappaMax = 100.0;
+
 // Internal plan flag (above the public SOS_FLAG_* bits): the plan of a
 // backward call, where channels without a horizon become single segments.
 constexpr int32_t kFlagBackwardPlan = 1 << 16;
@@ -85,6 +90,15 @@ struct __align__(16) Coef32 {
     float4 psi_pow[4];    // Psi^(2^r), r = 0..3 (warp scan)
     float4 psi_w[16];     // Psi^w, w = 0..15 (fold the tile state into warp w)
     float4 lane_pow[32];  // Phi^l, l = 0..31 (fold the warp state into lane l)
+    // cyclic reduction (Sec. VI-C), built when the call asks for it: level i
+    // of log2 N has (e_i, f_i, g_i = f_i / e_i, c_i = e_i - g_i) and
+    // d_i = -f_i g_i (Eq. cr_coeff_update); the terminal recurrence across
+    // lanes Y_l + e_n Y_{l-1} + f_n Y_{l-2} = V_l (Eq. cr_terminal_block) is
+    // scanned with the powers C^(2^j) of C = [[-e_n, -f_n], [1, 0]].
+    float4 cr_lv[6];      // (e_i, f_i, g_i, c_i)
+    float4 cr_d[2];       // d_0 .. d_7
+    float4 cr_tpow[5];    // C^(2^j), row-major
+    float4 cr_misc;       // e_n, f_n, kappa = max |g_i|, 1 if CR is used for this section
 };
 
 // Per (channel, section) double-float powers of the tile transition
@@ -157,7 +171,7 @@ struct Params {
     int32_t N;           // samples per lane
     int32_t W;           // warps per tile
     int32_t flags_opt;   // SOS_FLAG_*
-    int32_t pad;
+    int32_t algo;        // recursive-stage solver: 1 PH, 2 CR where well conditioned
     int64_t seg;         // pipeline segment length (samples, a multiple of 32 N)
     float* inter;        // [kmax][total] section outputs (backward's forward pass), or null
     const float* gy;     // backward: dL/dy [total]

@@ -52,6 +52,7 @@ struct PipeShared {
     unsigned long long bar[kPipeRing][kPipeStages];  // slot ready for stage j
     unsigned long long free_[kPipeRing];             // slot free for the loader
     float4 phi[kMaxSections][5];                     // section k's Phi^(2^j), staged by warp 1 + k
+    float4 cr[kMaxSections][14];                     // section k's cyclic-reduction coefficients
 };
 
 // try_wait with a suspend-time hint: a warp whose slot is not ready yet

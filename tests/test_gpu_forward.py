@@ -301,3 +301,32 @@ def test_long_and_short_memory_channels_in_one_batch():
     err = oracle.rel_l2_per_channel(y, y_ref, np.array(lengths))
     print("long-memory rel-L2", err[0:5:2], "short", err[1::2])
     assert err[1::2].max() <= 1e-5 and err[0:5:2].max() <= 1e-3
+
+
+@pytest.mark.parametrize("N", [16, 32, 64])
+def test_cyclic_reduction_ragged_multichannel(N):
+    """The cyclic-reduction solver (algo 2) on the ragged cases."""
+    T = N * 32 * 8
+    lengths = [1, 2, 3, N - 1, N, N + 1, 32 * N - 1, 32 * N + 1, T - 1, T + 1, 3 * T + 5, 0,
+               7 * T + 333]
+    args = random_case(400 + N, lengths, 8)
+    y_ref, zf_ref = run_oracle(*args)
+    y, zf = run_gpu(args, tuning=(N, 8, 2, 0))
+    check(y, zf, y_ref, zf_ref, np.array(lengths), args[2].numpy(), 1e-5)
+
+
+def test_cyclic_reduction_ill_conditioned_level_keeps_ph():
+    """A pole pair at angle pi/4 makes e_1 = -2 r^2 cos(2 theta) vanish at
+    the second reduction level (g_1 = f_1 / e_1 unbounded): that section
+    must be solved by PH, the others by CR, with the same accuracy."""
+    r = 0.9
+    bad = [1.0, 0.0, -1.0, 1.0, -2 * r * np.cos(np.pi / 4), r * r]
+    lengths = [100_000, 33_333]
+    x, sos, K, L, zi = random_case(500, lengths, 4)
+    sos[:, 1] = torch.tensor(bad, dtype=torch.float64)
+    K[:] = 4
+    args = (x, sos, K, L, zi)
+    y_ref, zf_ref = run_oracle(*args)
+    for N in (16, 32, 64):
+        y, zf = run_gpu(args, tuning=(N, 8, 2, 0))
+        check(y, zf, y_ref, zf_ref, np.array(lengths), K.numpy(), 1e-5)
