@@ -1,10 +1,14 @@
 #!/usr/bin/env python3
 """Benchmark of the cascaded-biquad hot path on GB300.
 
-One step = one full call of the C ABI's sos_filter (plan kernel + fused
-filtering kernel) on the 16th-order (K = 8) Butterworth band-pass workload,
-2^24 FP32 samples i.i.d. N(0, 1), one channel, zero initial state, inputs
-resident in HBM.  Prints one JSON line (rank 0).
+One step = one full call of the C ABI's sos_filter on the 16th-order (K = 8)
+Butterworth band-pass workload, 2^24 FP32 samples i.i.d. N(0, 1), one
+channel, zero initial state, inputs resident in HBM: sos_prepare (plan and
+dispatch-order kernels) then sos_apply (section-pipeline kernel, then the
+look-back kernel, which finds no carried channel here).  The tuning (N, W,
+solver) is chosen by the library's autotuner before the timed region.
+Prints one JSON line (rank 0), with the batched (4096 channels) and
+differentiation (forward + backward, 256 x 2^16) workloads as extra fields.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -205,7 +209,7 @@ def run_reference(args):
     return 0
 
 
-def end_to_end(P, x, sos, stream, samples, world, args):
+def end_to_end(P, x, sos, stream, samples, world, args, tuning):
     """Same metric through the public API with host buffers: pinned host
     input -> device -> sosfilt -> host output, every step."""
     import torch
@@ -216,7 +220,7 @@ def end_to_end(P, x, sos, stream, samples, world, args):
     e_steps = max(3, min(args.steps, 10))
     for _ in range(2):
         xd.copy_(xh, non_blocking=True)
-        step_e2e_y = P.sosfilt(xd, sos)
+        step_e2e_y = P.sosfilt(xd, sos, tuning=tuning)
         yh.copy_(step_e2e_y[0], non_blocking=True)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -224,7 +228,7 @@ def end_to_end(P, x, sos, stream, samples, world, args):
     e0.record(stream)
     for _ in range(e_steps):
         xd.copy_(xh, non_blocking=True)
-        yd, zfd = P.sosfilt(xd, sos)
+        yd, zfd = P.sosfilt(xd, sos, tuning=tuning)
         yh.copy_(yd, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -233,6 +237,100 @@ def end_to_end(P, x, sos, stream, samples, world, args):
     e2e_value = samples * world / (e2e_ms * 1e-3) / 1e9
     return e2e_value, e2e_ms
 
+
+
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sos_pipe_kernel_bp16_2e24.json")
+PIPE_SOURCES = ["pipe.cu", "pipe_section.cuh", "sos_pipe.cuh", "sos_async.cuh", "sos_kernels.cuh",
+                "sos_common.cuh"]
+
+
+def pipe_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in PIPE_SOURCES:
+        with open(os.path.join(ROOT, "paper_2607_14054_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(samples: int):
+    """DRAM bytes per pipeline launch from the committed ncu summary, scaled
+    to this workload's samples; None when the kernel sources changed since."""
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            prof = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if prof.get("source_hash") != pipe_source_hash():
+        return None
+    return prof["dram_bytes_per_launch"] * samples / prof["samples"]
+
+
+def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
+    """4096 channels, lengths U[2^10, 2^20], K U{1..8}, random sections,
+    nonzero zi: one prepare + apply per step, inputs resident."""
+    import torch
+    from synth import workloads
+    from paper_2607_14054_gb300.autotune import autotune
+    wl = workloads.batched(device=dev)
+    tuning = autotune(wl.x, wl.sos, wl.K, wl.lengths, wl.zi)
+    plan = P.SosFilter(wl.lengths, wl.kmax, tuning=tuning, device=dev)
+    y = torch.empty_like(wl.x)
+    zf = torch.empty(wl.n_channels, wl.kmax, 2, device=dev)
+    for _ in range(2):
+        plan(wl.x, wl.sos, wl.K, wl.zi, y=y, zf=zf)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan(wl.x, wl.sos, wl.K, wl.zi, y=y, zf=zf)
+    e1.record()
+    torch.cuda.synchronize()
+    if plan.device_status() != 0:
+        raise RuntimeError("batched leg: device status")
+    ms = reduce_max(e0.elapsed_time(e1) / steps, world)
+    total = wl.total
+    lens = wl.lengths.double()
+    fma = float((lens * (6 * wl.K.cpu().double() + 1)).sum())
+    t_hbm = 8.0 * total / (hbm_gbs * 1e9)
+    t_alu = fma / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
+    roof = total / max(t_hbm, t_alu) / 1e9
+    value = total * world / (ms * 1e-3) / 1e9
+    return {"workload": wl.name, "channels": wl.n_channels, "samples": total,
+            "value": value, "unit": "Gsamples/s", "ms_per_step": ms,
+            "roofline_gsamples_per_s": roof, "frac_of_roofline": value / world / roof,
+            "bound": "hbm" if t_hbm >= t_alu else "alu", "tuning": list(tuning),
+            "step": "sos_filter (prepare + apply)"}
+
+
+def backward_leg(P, dev, world, steps: int = 5):
+    """256 x 2^16, K = 8: forward + backward through the autograd Function."""
+    import torch
+    from synth import workloads
+    wl = workloads.differentiation(device=dev)
+    xg = wl.x.clone().requires_grad_(True)
+    sg = wl.sos.clone().requires_grad_(True)
+    zg = wl.zi.clone().requires_grad_(True)
+    tgt = torch.zeros_like(wl.x)
+
+    def fb():
+        y, zf = P.sosfilt_diff(xg, sg, wl.K, lengths=wl.lengths, zi=zg)
+        loss = ((y - tgt) ** 2).mean()
+        loss.backward()
+
+    for _ in range(2):
+        fb()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fb()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = reduce_max(e0.elapsed_time(e1) / steps, world)
+    return {"workload": wl.name, "samples": wl.total,
+            "value": wl.total * world / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+            "ms_per_step": ms, "step": "forward + MSE + backward (dL/dx, dL/dsos, dL/dzi)"}
 
 
 def main():
@@ -246,6 +344,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling)")
     ap.add_argument("--clock-seconds", type=float, default=2.0)
     ap.add_argument("--clocks-out", default="")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the batched and differentiation legs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -261,8 +361,11 @@ def main():
 
     wl = workloads.plain_bandpass16(n=1 << 24, device=dev)
     Kmax = wl.kmax
-    tuning = tuple(int(v) for v in args.tuning.split(",")) + (0, 0) if args.tuning else None
-    tuning = tuning[:4] if tuning else None
+    if args.tuning:
+        tuning = (tuple(int(v) for v in args.tuning.split(",")) + (0, 0, 0, 0))[:4]
+    else:
+        from paper_2607_14054_gb300.autotune import autotune
+        tuning = autotune(wl.x, wl.sos, wl.K, wl.lengths, None)
     plan = P.SosFilter(wl.lengths, Kmax, tuning=tuning, device=dev)
     x = wl.x
     sos = wl.sos
@@ -286,22 +389,27 @@ def main():
     with torch.cuda.stream(side):
         step()
     torch.cuda.current_stream(dev).wait_stream(side)
-    g_prep, g_apply = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    # sos_apply is sos_apply_pipeline then sos_apply_carried: captured as two
+    # graphs so that events on the launching stream time the pipeline kernel
+    g_prep, g_pipe, g_carry = (torch.cuda.CUDAGraph() for _ in range(3))
     with torch.cuda.graph(g_prep):
         plan.prepare(sos, K)
-    with torch.cuda.graph(g_apply):
-        plan.apply(x, y, None, zf)
+    with torch.cuda.graph(g_pipe):
+        plan.apply_part("pipeline", x, y, None, zf)
+    with torch.cuda.graph(g_carry):
+        plan.apply_part("carried", x, y, None, zf)
     torch.cuda.synchronize()
 
     def step():  # noqa: F811 - the captured form of the same step
         g_prep.replay()
-        g_apply.replay()
+        g_pipe.replay()
+        g_carry.replay()
     st = plan.device_status()
     if st != 0:
         raise RuntimeError(f"device status {st} after warm-up")
 
     stream = torch.cuda.current_stream(dev)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     barrier(world)
     torch.cuda.synchronize()
     t_wall0 = time.perf_counter()
@@ -310,16 +418,20 @@ def main():
         ev[i][0].record(stream)
         g_prep.replay()
         ev[i][1].record(stream)
-        g_apply.replay()
+        g_pipe.replay()
         ev[i][2].record(stream)
+        g_carry.replay()
+        ev[i][3].record(stream)
     torch.cuda.synchronize()
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
-    apply_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[3]) for e in ev]
+    apply_ms = [e[1].elapsed_time(e[3]) for e in ev]
+    pipe_ms = [e[1].elapsed_time(e[2]) for e in ev]
     prep_ms = [e[0].elapsed_time(e[1]) for e in ev]
     ms_per_step = sum(step_ms) / len(step_ms)
     ms_apply = sum(apply_ms) / len(apply_ms)
+    ms_pipe = reduce_max(sum(pipe_ms) / len(pipe_ms), world)
     ms_per_step = reduce_max(ms_per_step, world)
     ms_apply = reduce_max(ms_apply, world)
     samples = wl.total
@@ -343,7 +455,7 @@ def main():
     # filter -> host output, every step
     e2e_value, e2e_ms = None, None
     if not args.no_e2e:
-        e2e_value, e2e_ms = end_to_end(P, x, sos, stream, samples, world, args)
+        e2e_value, e2e_ms = end_to_end(P, x, sos, stream, samples, world, args, plan.tuning)
 
     # quick parity sanity
     # quick parity sanity on a prefix (causal: the first n outputs of the full
@@ -365,9 +477,13 @@ def main():
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     fmas = fma_per_sample(8)
-    achieved = 2.0 * fmas * samples / (ms_apply * 1e-3) / 1e12
+    achieved = 2.0 * fmas * samples / (ms_pipe * 1e-3) / 1e12
+    traffic = profiled_traffic(samples)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     roof_samples = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / fmas) / 1e9
+
+    batched = None if args.no_extra else batched_leg(P, dev, world, sms, sm_max, hbm_gbs)
+    backward = None if args.no_extra else backward_leg(P, dev, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -388,21 +504,27 @@ def main():
         "data": "synthetic",
         "config": {"workload": wl.name, "samples": samples, "channels": 1, "sections": 8,
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
-                   "tuning": list(plan.tuning), "step": "sos_prepare + sos_apply (CUDA-graph replays)",
+                   "tuning": list(plan.tuning),
+                   "tuning_source": "--tuning" if args.tuning else "autotuner (untimed setup)",
+                   "step": "sos_prepare + sos_apply (CUDA-graph replays: plan, order, "
+                           "pipeline, look-back kernels)",
                    "ms_prepare": sum(prep_ms) / len(prep_ms), "ms_apply": ms_apply,
+                   "ms_pipeline_kernel": ms_pipe,
                    "roofline_gsamples_per_s": roof_samples,
                    "frac_of_sample_roofline": value / world / roof_samples,
                    "wall_s_timed": t_wall},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
-                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
-                     "kernel": "sos_forward_kernel", "flops_per_sample": 2 * fmas,
+                     "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
+                     "kernel": "sos_pipe_kernel", "flops_per_sample": 2 * fmas,
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz ({src} max clock)"},
         "e2e": None if e2e_value is None else {
             "value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
             "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
             "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)"},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 4 * args.steps,
+        "batched": batched,
+        "backward": backward,
         "clocks": clocks,
         "parity_rel_l2_prefix": parity,
         "cpu_baseline": cpu,

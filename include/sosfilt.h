@@ -154,6 +154,23 @@ sos_status sos_apply(const float *x, int32_t n_channels, int32_t kmax,
                      const int64_t *lengths_host, const float *zi, float *y, float *zf,
                      void *workspace, size_t ws_bytes, const sos_tuning *tuning, void *stream);
 
+/* The two launches of sos_apply, separately: the section pipeline (channels
+ * within their memory horizon) and the look-back kernel (channels whose
+ * state is carried between tiles; it also writes the final states of empty
+ * channels and of sections past K).  sos_apply = sos_apply_pipeline then
+ * sos_apply_carried on the same stream; the two touch disjoint channels, so
+ * they may also run on two streams (both after sos_prepare, both before the
+ * outputs are read).  Same arguments and errors as sos_apply.  No
+ * counterpart in the paper: a scheduling split of the one operation. */
+sos_status sos_apply_pipeline(const float *x, int32_t n_channels, int32_t kmax,
+                              const int64_t *lengths_host, const float *zi, float *y, float *zf,
+                              void *workspace, size_t ws_bytes, const sos_tuning *tuning,
+                              void *stream);
+sos_status sos_apply_carried(const float *x, int32_t n_channels, int32_t kmax,
+                             const int64_t *lengths_host, const float *zi, float *y, float *zf,
+                             void *workspace, size_t ws_bytes, const sos_tuning *tuning,
+                             void *stream);
+
 /* sos_filter without a caller-allocated workspace (the paper has no
  * counterpart; this is a deployment convenience).  Some callers cannot call
  * cudaMalloc at all: real-time audio or control callbacks where its latency

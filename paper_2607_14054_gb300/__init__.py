@@ -179,6 +179,19 @@ class SosFilter:
             raise SosError(st, "sos_plan_query")
         return h, t
 
+    def apply_part(self, part: str, x: torch.Tensor, y: torch.Tensor,
+                   zi: Optional[torch.Tensor] = None, zf: Optional[torch.Tensor] = None):
+        """One of the two launches of apply(): "pipeline" or "carried"."""
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_apply_part(part, x.data_ptr(), self.n_channels, self.kmax,
+                                 self.lengths_host.data_ptr(),
+                                 zi.data_ptr() if zi is not None else 0, y.data_ptr(),
+                                 zf.data_ptr() if zf is not None else 0, self.workspace.data_ptr(),
+                                 self.ws_bytes, self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_apply_" + part)
+        return y, zf
+
     def device_status(self) -> int:
         """Synchronises the current stream and returns the device-side status
         of the latest call (0 = OK)."""
@@ -192,7 +205,8 @@ _plans = {}
 def sosfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
             lengths=None, zi: Optional[torch.Tensor] = None, tuning=None, check: bool = False):
     """Filter x (float32, CUDA, packed channels) through the cascade ``sos``
-    (float64 [C, kmax, 6] or [kmax, 6]).  Returns (y, zf)."""
+    (float64 [C, kmax, 6] or [kmax, 6]).  Returns (y, zf).  ``tuning="auto"``
+    picks (N, W, solver) for these shapes by measurement (``autotune``)."""
     _check_device(x, "x")
     if sos.dim() == 2:
         sos = sos.unsqueeze(0)
@@ -201,6 +215,11 @@ def sosfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None
         if C != 1:
             raise ValueError("lengths are required for more than one channel")
         lengths = [x.numel()]
+    if isinstance(tuning, str):
+        if tuning != "auto":
+            raise ValueError("tuning must be a 4-tuple, None or 'auto'")
+        from .autotune import autotune
+        tuning = autotune(x, sos, K, lengths, zi)
     lh = tuple(int(v) for v in torch.as_tensor(lengths).reshape(-1).tolist())
     key = (x.device, lh, kmax, tuple(tuning) if tuning is not None else None)
     plan = _plans.get(key)

@@ -73,6 +73,9 @@ def load(build_if_missing: bool = False):
         lib.sos_prepare.restype = ctypes.c_int
         lib.sos_apply.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
         lib.sos_apply.restype = ctypes.c_int
+        for fn in (lib.sos_apply_pipeline, lib.sos_apply_carried):
+            fn.argtypes = [vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
+            fn.restype = ctypes.c_int
         lib.sos_filter_static.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, tp, vp,
                                           ctypes.POINTER(ctypes.c_int32)]
         lib.sos_filter_static.restype = ctypes.c_int
@@ -127,6 +130,15 @@ def sos_apply(x, n_channels, kmax, lengths_host, zi, y, zf, ws, ws_bytes, tuning
     V = ctypes.c_void_p
     return int(load().sos_apply(V(x), n_channels, kmax, V(lengths_host), V(zi or None), V(y),
                                 V(zf or None), V(ws), ws_bytes, _tuning(tuning), V(stream)))
+
+
+def sos_apply_part(part: str, x, n_channels, kmax, lengths_host, zi, y, zf, ws, ws_bytes,
+                   tuning, stream) -> int:
+    """part: "pipeline" or "carried"; pointer arguments are integers."""
+    V = ctypes.c_void_p
+    fn = load().sos_apply_pipeline if part == "pipeline" else load().sos_apply_carried
+    return int(fn(V(x), n_channels, kmax, V(lengths_host), V(zi or None), V(y), V(zf or None),
+                  V(ws), ws_bytes, _tuning(tuning), V(stream)))
 
 
 def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y, zf, tuning,

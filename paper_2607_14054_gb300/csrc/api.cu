@@ -180,9 +180,17 @@ sos_status sos_prepare(const double* sos, const int32_t* K, int32_t n_channels, 
     return SOS_OK;
 }
 
-sos_status sos_apply(const float* x, int32_t n_channels, int32_t kmax,
-                     const int64_t* lengths_host, const float* zi, float* y, float* zf,
-                     void* workspace, size_t ws_bytes, const sos_tuning* tuning, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// which of the two filtering launches a call enqueues
+enum ApplyParts { kPartPipe = 1, kPartCarry = 2 };
+
+sos_status apply_parts(const float* x, int32_t n_channels, int32_t kmax,
+                       const int64_t* lengths_host, const float* zi, float* y, float* zf,
+                       void* workspace, size_t ws_bytes, const sos_tuning* tuning, void* stream,
+                       int parts) {
     Params p{};
     int64_t tiles = 0, total = 0;
     const sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p,
@@ -202,15 +210,44 @@ sos_status sos_apply(const float* x, int32_t n_channels, int32_t kmax,
     // the section pipeline for channels within their memory horizon, then
     // the look-back kernel for the others (which also writes the final states
     // of empty channels and unused sections: at least one CTA)
-    if (total > 0) {
+    if (total > 0 && (parts & kPartPipe)) {
         const int64_t grid = (int64_t)(device_sms() > 0 ? device_sms() : 1) * kPipeCtasPerSm;
         if (launch_pipe(p, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
             return SOS_ERR_CUDA;
     }
-    const int64_t launch_tiles = tiles > 0 ? tiles : 1;
-    if (launch_forward(p, launch_tiles, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-        return SOS_ERR_CUDA;
+    if (parts & kPartCarry) {
+        const int64_t launch_tiles = tiles > 0 ? tiles : 1;
+        if (launch_forward(p, launch_tiles, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+            return SOS_ERR_CUDA;
+    }
     return SOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sos_status sos_apply(const float* x, int32_t n_channels, int32_t kmax,
+                     const int64_t* lengths_host, const float* zi, float* y, float* zf,
+                     void* workspace, size_t ws_bytes, const sos_tuning* tuning, void* stream) {
+    return apply_parts(x, n_channels, kmax, lengths_host, zi, y, zf, workspace, ws_bytes, tuning,
+                       stream, kPartPipe | kPartCarry);
+}
+
+sos_status sos_apply_pipeline(const float* x, int32_t n_channels, int32_t kmax,
+                              const int64_t* lengths_host, const float* zi, float* y, float* zf,
+                              void* workspace, size_t ws_bytes, const sos_tuning* tuning,
+                              void* stream) {
+    return apply_parts(x, n_channels, kmax, lengths_host, zi, y, zf, workspace, ws_bytes, tuning,
+                       stream, kPartPipe);
+}
+
+sos_status sos_apply_carried(const float* x, int32_t n_channels, int32_t kmax,
+                             const int64_t* lengths_host, const float* zi, float* y, float* zf,
+                             void* workspace, size_t ws_bytes, const sos_tuning* tuning,
+                             void* stream) {
+    return apply_parts(x, n_channels, kmax, lengths_host, zi, y, zf, workspace, ws_bytes, tuning,
+                       stream, kPartCarry);
 }
 
 sos_status sos_filter(const float* x, const double* sos, const int32_t* K, int32_t n_channels,

@@ -408,6 +408,11 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
         }
     }
 
+    // No carried channel in this call (every channel within its horizon goes
+    // through the section pipeline): nothing to dispatch, no slot written, so
+    // neither the tile counter nor the look-back epoch has to move.
+    if (total == 0) return;
+
     // Tiles are reserved one ahead: while tile d computes from one buffer,
     // the copies of the next reserved tile fill the other.  A CTA still
     // processes its tiles in dispatch order, and the lowest unfinished tile
