@@ -4,9 +4,11 @@
 One step = one full call of the C ABI's sos_filter on the 16th-order (K = 8)
 Butterworth band-pass workload, 2^24 FP32 samples i.i.d. N(0, 1), one
 channel, zero initial state, inputs resident in HBM: sos_prepare (plan and
-dispatch-order kernels) then sos_apply (section-pipeline kernel, then the
-look-back kernel, which finds no carried channel here).  The tuning (N, W,
-solver) is chosen by the library's autotuner before the timed region.
+dispatch-order kernels) then sos_apply (the kernel for channels within their
+memory horizon -- warp segments by default, or the section pipeline -- then
+the look-back kernel, which finds no carried channel here).  The tuning (N,
+W, solver, kernel) is chosen by the library's autotuner before the timed
+region.
 Prints one JSON line (rank 0), with the batched (4096 channels) and
 differentiation (forward + backward, 256 x 2^16) workloads as extra fields.
 
@@ -239,29 +241,39 @@ def end_to_end(P, x, sos, stream, samples, world, args, tuning):
 
 
 
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "sos_pipe_kernel_bp16_2e24.json")
-PIPE_SOURCES = ["pipe.cu", "pipe_section.cuh", "sos_pipe.cuh", "sos_async.cuh", "sos_kernels.cuh",
-                "sos_common.cuh"]
+# the kernel for channels within their memory horizon: its committed ncu
+# summary and the sources it is built from
+_COMMON_SOURCES = ["pipe_section.cuh", "sos_pipe.cuh", "sos_async.cuh", "sos_kernels.cuh",
+                   "sos_common.cuh"]
+KERNEL_PROFILES = {
+    "sos_warpseg_kernel": ("sos_warpseg_kernel_bp16_2e24.json", ["warpseg.cu"] + _COMMON_SOURCES),
+    "sos_pipe_kernel": ("sos_pipe_kernel_bp16_2e24.json", ["pipe.cu"] + _COMMON_SOURCES),
+}
 
 
-def pipe_source_hash() -> str:
+def horizon_kernel(tuning) -> str:
+    return "sos_pipe_kernel" if int(tuning[3]) & 4 else "sos_warpseg_kernel"
+
+
+def source_hash(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for name in PIPE_SOURCES:
+    for name in KERNEL_PROFILES[kernel][1]:
         with open(os.path.join(ROOT, "paper_2607_14054_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(samples: int):
-    """DRAM bytes per pipeline launch from the committed ncu summary, scaled
-    to this workload's samples; None when the kernel sources changed since."""
+def profiled_traffic(kernel: str, samples: int):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary,
+    scaled to this workload's samples; None when the kernel's sources changed
+    since the counters were taken."""
     try:
-        with open(PROFILE_SUMMARY) as f:
+        with open(os.path.join(ROOT, "profiles", KERNEL_PROFILES[kernel][0])) as f:
             prof = json.load(f)
     except (OSError, ValueError):
         return None
-    if prof.get("source_hash") != pipe_source_hash():
+    if prof.get("source_hash") != source_hash(kernel):
         return None
     return prof["dram_bytes_per_launch"] * samples / prof["samples"]
 
@@ -389,8 +401,9 @@ def main():
     with torch.cuda.stream(side):
         step()
     torch.cuda.current_stream(dev).wait_stream(side)
-    # sos_apply is sos_apply_pipeline then sos_apply_carried: captured as two
-    # graphs so that events on the launching stream time the pipeline kernel
+    # sos_apply is sos_apply_pipeline (the horizon kernel) then
+    # sos_apply_carried: captured as two graphs so that events on the
+    # launching stream time the horizon kernel alone
     g_prep, g_pipe, g_carry = (torch.cuda.CUDAGraph() for _ in range(3))
     with torch.cuda.graph(g_prep):
         plan.prepare(sos, K)
@@ -478,7 +491,8 @@ def main():
     peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     fmas = fma_per_sample(8)
     achieved = 2.0 * fmas * samples / (ms_pipe * 1e-3) / 1e12
-    traffic = profiled_traffic(samples)
+    kname = horizon_kernel(plan.tuning)
+    traffic = profiled_traffic(kname, samples)
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     roof_samples = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / fmas) / 1e9
 
@@ -507,15 +521,15 @@ def main():
                    "tuning": list(plan.tuning),
                    "tuning_source": "--tuning" if args.tuning else "autotuner (untimed setup)",
                    "step": "sos_prepare + sos_apply (CUDA-graph replays: plan, order, "
-                           "pipeline, look-back kernels)",
+                           "horizon, look-back kernels)",
                    "ms_prepare": sum(prep_ms) / len(prep_ms), "ms_apply": ms_apply,
-                   "ms_pipeline_kernel": ms_pipe,
+                   "horizon_kernel": kname, "ms_horizon_kernel": ms_pipe,
                    "roofline_gsamples_per_s": roof_samples,
                    "frac_of_sample_roofline": value / world / roof_samples,
                    "wall_s_timed": t_wall},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_tflops,
                      "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
-                     "kernel": "sos_pipe_kernel", "flops_per_sample": 2 * fmas,
+                     "kernel": kname, "flops_per_sample": 2 * fmas,
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz ({src} max clock)"},
         "e2e": None if e2e_value is None else {

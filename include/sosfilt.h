@@ -72,23 +72,35 @@ typedef enum sos_status {
  *   algo:     recursive-stage solver: 0 = default (PH), 1 = PH (Sec. VI-B),
  *             2 = cyclic reduction (Sec. VI-C) for every section whose
  *             reduction is well conditioned (max |f_i / e_i| <= 100 over the
- *             log2 N levels; the others keep PH).  CR applies to channels run
- *             by the section pipeline; channels carried by the look-back use PH.
+ *             log2 N levels; the others keep PH).  CR applies to channels
+ *             within their memory horizon (the warp-segment kernel takes CR
+ *             for a channel only when all its sections qualify, the section
+ *             pipeline section by section); channels carried by the look-back
+ *             use PH.
  *   flags:    bit 0 (SOS_FLAG_CHECK_STABLE): reject sections whose poles are
  *             not strictly inside the unit circle.
  *             bit 1 (SOS_FLAG_CARRY_ONLY): carry every channel's state between
  *             tiles by the decoupled look-back, even where the channel's
  *             memory horizon would let its tiles overlap and start from zero
  *             state (same results to rounding; for testing and tuning).
+ *             bit 2 (SOS_FLAG_SECTION_PIPELINE): run the channels within their
+ *             memory horizon by the section pipeline (one warp per section,
+ *             groups handed from warp to warp, segments sized per CTA)
+ *             instead of the default warp-segment kernel (one warp filters a
+ *             whole segment through all K sections, segments sized to give
+ *             every resident warp work).  Segment lengths differ, so the same
+ *             flags must reach sos_prepare and sos_apply.  The backward always
+ *             runs the section pipeline.
  *
  * Cross-tile state.  The plan bounds each channel's impulse-response tail by
  * partial fractions over its poles and finds its memory horizon P: the warm-up
  * after which the state a tile would drop changes the output by less than
- * 2^-30 relative.  If P <= T/2, the channel's tiles overlap by P samples and
- * each starts from zero state (no cross-tile dependency); otherwise (poles
- * near or on the unit circle, coincident poles) the DF2T state of every
- * section is carried by a decoupled look-back composing FP64-accurate affine
- * maps (Sec. V's group hand-off made parallel). */
+ * 2^-30 relative.  If P <= S/2 (S the segment length, a multiple of 32 N
+ * chosen from the call's total length), the channel is cut into segments that
+ * each start P samples early from zero state (no cross-segment dependency);
+ * otherwise (poles near or on the unit circle, coincident poles) the DF2T
+ * state of every section is carried by a decoupled look-back composing
+ * FP64-accurate affine maps (Sec. V's group hand-off made parallel). */
 typedef struct sos_tuning {
     int32_t n_blocks;
     int32_t warps;
@@ -98,6 +110,7 @@ typedef struct sos_tuning {
 
 #define SOS_FLAG_CHECK_STABLE 1
 #define SOS_FLAG_CARRY_ONLY 2
+#define SOS_FLAG_SECTION_PIPELINE 4
 #define SOS_MAX_SECTIONS 8
 
 /* Bytes of device workspace needed for a call with these sizes.
@@ -154,8 +167,9 @@ sos_status sos_apply(const float *x, int32_t n_channels, int32_t kmax,
                      const int64_t *lengths_host, const float *zi, float *y, float *zf,
                      void *workspace, size_t ws_bytes, const sos_tuning *tuning, void *stream);
 
-/* The two launches of sos_apply, separately: the section pipeline (channels
- * within their memory horizon) and the look-back kernel (channels whose
+/* The two launches of sos_apply, separately: the kernel for channels within
+ * their memory horizon (the warp-segment kernel, or the section pipeline
+ * under SOS_FLAG_SECTION_PIPELINE) and the look-back kernel (channels whose
  * state is carried between tiles; it also writes the final states of empty
  * channels and of sections past K).  sos_apply = sos_apply_pipeline then
  * sos_apply_carried on the same stream; the two touch disjoint channels, so

@@ -19,6 +19,7 @@ _lib = None
 SOS_OK = 0
 SOS_FLAG_CHECK_STABLE = 1
 SOS_FLAG_CARRY_ONLY = 2
+SOS_FLAG_SECTION_PIPELINE = 4
 SOS_MAX_SECTIONS = 8
 
 STATUS_NAMES = {

@@ -1,4 +1,4 @@
-"""Per-shape choice of the kernel tuning (N, W, solver) by measurement.
+"""Per-shape choice of the kernel tuning (N, W, solver, kernel) by measurement.
 
 The sequential depth of a section grows with N (PH: N, cyclic reduction:
 log2 N) while the lane scan's cost per sample shrinks with it, and which one
@@ -42,16 +42,21 @@ def shape_key(lengths: Sequence[int], kmax: int, carried: bool) -> Tuple:
     return (int(kmax), lb, cb, "carried" if carried else "horizon")
 
 
+KERNELS = (0, 4)  # warp segments, section pipeline (SOS_FLAG_SECTION_PIPELINE)
+
+
 def candidates(carried: bool) -> List[Tuple[int, int, int, int]]:
-    """Tunings to try: every N with both solvers; several W only when some
-    channel is carried by the look-back (W sizes the look-back tiles)."""
+    """Tunings to try: every N with both solvers and both kernels for the
+    channels within their memory horizon; several W only when some channel
+    is carried by the look-back (W sizes the look-back tiles)."""
     out = []
     for n in (16, 32, 64):
         ws = sorted({w for (nn, w) in SUPPORTED_NW if nn == n}) if carried else \
             [8 if (n, 8) in SUPPORTED_NW else min(w for (nn, w) in SUPPORTED_NW if nn == n)]
         for w in ws:
             for a in ALGOS:
-                out.append((n, w, a, 0))
+                for f in KERNELS:
+                    out.append((n, w, a, f))
     return out
 
 

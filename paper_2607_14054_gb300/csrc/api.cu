@@ -11,6 +11,9 @@ cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream);
 cudaError_t launch_adjoint(const Params& p, int64_t grid, double* grad_sos, cudaStream_t stream);
 bool forward_supported(int N, int W);
 bool pipe_supported(int N);
+cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream);
+int warpseg_ctas_per_sm(int N);
+int warpseg_warps_per_cta();
 }  // namespace sosf
 
 using namespace sosf;
@@ -50,15 +53,23 @@ int device_sms() {
 
 constexpr int kPipeCtasPerSm = 2;
 
-// Pipeline segment length: long enough that the warm-up before each segment
-// is a small fraction of it, short enough that the segments of the whole
-// call keep every pipeline CTA busy (between 8 and 64 groups of 32 N).
-int64_t segment_length(int64_t total_len, int N) {
+// Segment length: long enough that the warm-up before each segment is a small
+// fraction of it, short enough that the segments of the whole call keep every
+// consumer busy: each pipeline CTA (between 8 and 64 groups of 32 N), or, for
+// the warp-segment kernel, each resident warp (at least 8192 samples, so that
+// horizons up to 4096 samples qualify as with the pipeline, and at most 64
+// groups).
+int64_t segment_length(int64_t total_len, int N, bool warp_segments) {
     const int64_t group = 32LL * N;
-    const int sms = device_sms();
-    const int64_t ctas = (int64_t)(sms > 0 ? sms : 148) * kPipeCtasPerSm;
-    int64_t g = (total_len + ctas * group - 1) / (ctas * group);
-    if (g < 8) g = 8;
+    const int sms = device_sms() > 0 ? device_sms() : 148;
+    int64_t units = (int64_t)sms * kPipeCtasPerSm, gmin = 8;
+    if (warp_segments) {
+        const int occ = warpseg_ctas_per_sm(N);
+        units = (int64_t)sms * (occ > 0 ? occ : 1) * warpseg_warps_per_cta();
+        gmin = (8192 + group - 1) / group;
+    }
+    int64_t g = (total_len + units * group - 1) / (units * group);
+    if (g < gmin) g = gmin;
     if (g > 64) g = 64;
     return g * group;
 }
@@ -153,7 +164,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->W = tu.W;
     p->flags_opt = tu.flags;
     p->algo = tu.algo;
-    p->seg = segment_length(total_len, tu.N);
+    p->seg = segment_length(total_len, tu.N, (tu.flags & SOS_FLAG_SECTION_PIPELINE) == 0);
     p->total = total_len;
     *tiles_out = tiles;
     *total_len_out = total_len;
@@ -207,13 +218,17 @@ sos_status apply_parts(const float* x, int32_t n_channels, int32_t kmax,
     p.y = y;
     p.zi = zi;
     p.zf = zf;
-    // the section pipeline for channels within their memory horizon, then
-    // the look-back kernel for the others (which also writes the final states
+    // the warp-segment kernel (or the section pipeline) for channels within
+    // their memory horizon, then the look-back kernel for the others (which also writes the final states
     // of empty channels and unused sections: at least one CTA)
     if (total > 0 && (parts & kPartPipe)) {
-        const int64_t grid = (int64_t)(device_sms() > 0 ? device_sms() : 1) * kPipeCtasPerSm;
-        if (launch_pipe(p, grid, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-            return SOS_ERR_CUDA;
+        const int64_t sms = device_sms() > 0 ? device_sms() : 1;
+        cudaError_t e;
+        if (p.flags_opt & SOS_FLAG_SECTION_PIPELINE)
+            e = launch_pipe(p, sms * kPipeCtasPerSm, static_cast<cudaStream_t>(stream));
+        else
+            e = launch_warpseg(p, sms * warpseg_ctas_per_sm(p.N), static_cast<cudaStream_t>(stream));
+        if (e != cudaSuccess) return SOS_ERR_CUDA;
     }
     if (parts & kPartCarry) {
         const int64_t launch_tiles = tiles > 0 ? tiles : 1;
@@ -389,7 +404,9 @@ sos_status sos_filter_backward(const float* x, const double* sos, const int32_t*
     p.sos = sos;
     p.K = K;
     p.lengths = lengths;
-    p.flags_opt |= kFlagBackwardPlan;
+    // the backward runs the section pipeline, on its segment length
+    p.flags_opt |= kFlagBackwardPlan | SOS_FLAG_SECTION_PIPELINE;
+    p.seg = segment_length(total, p.N, false);
     p.inter = reinterpret_cast<float*>(ws + BL.inter);
     p.gacc = reinterpret_cast<double*>(ws + BL.gacc);
     if (launch_plan(p, sm) != cudaSuccess) return SOS_ERR_CUDA;

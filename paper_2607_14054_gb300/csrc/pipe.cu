@@ -60,40 +60,63 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
     for (int g = 0; g < sg.ngroups; ++g) {
         pipe_wait(p, &sh.bar[s][k], use & 1u, lane);
         float* row = ring + s * SL::kFloats + lane * SL::kRow;
-        float v[N];
-#pragma unroll
-        for (int j = 0; j < N / 4; ++j) {
-            const float4 t = *reinterpret_cast<const float4*>(row + 4 * j);
-            v[4 * j + 0] = t.x;
-            v[4 * j + 1] = t.y;
-            v[4 * j + 2] = t.z;
-            v[4 * j + 3] = t.w;
-        }
         const bool zf_owner = g == g_last && lane == owner;
-        if (CR)
-            pipe_section_cr<N, FACT>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row, zf_dst,
-                                     FACT ? G : 1.f);
-        else
-            pipe_section<N, FACT>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
-                                  FACT ? G : 1.f);
-        if (p.inter) {
-            // the backward's forward pass: the true section output (times
-            // G_k when b0 is factored), for the segment's own samples
-            const int64_t gs = sg.cstart + (int64_t)g * (32 * N);
-            float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
-            const int64_t a = sg.out_lo - gs - lane * N, b = sg.out_hi - gs - lane * N;
+        const int64_t gs = sg.cstart + (int64_t)g * (32 * N);
+        if (!CR) {
+            float v[N];
 #pragma unroll
-            for (int m = 0; m < N; ++m)
-                if (m >= a && m < b) dst[m] = FACT ? v[m] * G : v[m];
+            for (int q = 0; q < N / 4; ++q) {
+                const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+                v[4 * q + 0] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+            pipe_section<N, FACT, true>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
+                                        FACT ? G : 1.f);
+            if (p.inter) {
+                float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
+                const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
+#pragma unroll
+                for (int m = 0; m < N; ++m)
+                    if (m >= lo && m < hi) dst[m] = FACT ? v[m] * G : v[m];
+            }
+            if (FACT && last_k) {
+#pragma unroll
+                for (int m = 0; m < N; ++m) v[m] *= G;
+            }
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q)
+                *reinterpret_cast<float4*>(row + 4 * q) =
+                    make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        } else {
+            float v[N];
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q) {
+                const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+                v[4 * q + 0] = t.x;
+                v[4 * q + 1] = t.y;
+                v[4 * q + 2] = t.z;
+                v[4 * q + 3] = t.w;
+            }
+            pipe_section_cr<N, FACT, true>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row,
+                                           zf_dst, FACT ? G : 1.f);
+            if (p.inter) {
+                float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
+                const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
+#pragma unroll
+                for (int m = 0; m < N; ++m)
+                    if (m >= lo && m < hi) dst[m] = FACT ? v[m] * G : v[m];
+            }
+            if (FACT && last_k) {
+#pragma unroll
+                for (int m = 0; m < N; ++m) v[m] *= G;
+            }
+#pragma unroll
+            for (int q = 0; q < N / 4; ++q)
+                *reinterpret_cast<float4*>(row + 4 * q) =
+                    make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
-        if (FACT && last_k) {
-#pragma unroll
-            for (int m = 0; m < N; ++m) v[m] *= G;
-        }
-#pragma unroll
-        for (int j = 0; j < N / 4; ++j)
-            *reinterpret_cast<float4*>(row + 4 * j) =
-                make_float4(v[4 * j + 0], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         __syncwarp();
         pipe_arrive(&sh.bar[s][k + 1]);
         if (++s == kPipeRing) {
@@ -131,11 +154,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             const float* src = p.x + sg.off + sg.cstart;
             int rem = (int)(sg.len - sg.cstart < 0x40000000 ? sg.len - sg.cstart : 0x40000000);
-            const bool aligned = (reinterpret_cast<uintptr_t>(src) & 15u) == 0;
             for (int g = 0; g < sg.ngroups; ++g, src += PC::kGroup, rem -= PC::kGroup) {
                 if (use > 0) pipe_wait(p, &sh.free_[s], (use - 1) & 1u, lane);
                 float* slot = ring + s * SL::kFloats;
-                if (rem >= PC::kGroup && aligned) {
+                if (rem >= PC::kGroup && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
                     const float4* s4 = reinterpret_cast<const float4*>(src);
 #pragma unroll
                     for (int q = 0; q < PC::kGran / 32; ++q)
@@ -158,7 +180,6 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
         for (int64_t d = blockIdx.x; d < total; d += gridDim.x) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             float* dst = p.y ? p.y + sg.off + sg.cstart : nullptr;
-            const bool aligned = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
             // group-relative store window [a, b)
             int a = (int)(sg.out_lo - sg.cstart);
             int b = (int)(sg.out_hi - sg.cstart);
@@ -168,6 +189,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
                 const float* slot = ring + s * SL::kFloats;
                 const int lo = a > 0 ? a : 0;
                 const int hi = b < PC::kGroup ? b : PC::kGroup;
+                const bool aligned = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
                 if (!p.y) {
                 } else if (lo == 0 && hi == PC::kGroup && aligned) {
                     float4* d4 = reinterpret_cast<float4*>(dst);

@@ -11,8 +11,11 @@ namespace sosf {
 
 // One section over one group, lane chunk v[] in registers, from the group's
 // incoming DF2T state (Z1, Z2) (scaled by 1/G_k when b0 is factored); leaves
-// the group's outgoing state in (Z1, Z2).
-template <int N, bool FACT>
+// the group's outgoing state in (Z1, Z2).  ZF: the group holds the channel's
+// last sample (at element mq of lane zf_owner's chunk), whose DF2T state goes
+// to zf_dst; a separate instantiation, since the run-time indexing it needs
+// costs registers that every other group would pay for.
+template <int N, bool FACT, bool ZF = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
@@ -24,7 +27,7 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     // a run-time index through the owner's scratch
     float xq = 0.f, xqm1 = 0.f;
     __syncwarp();
-    if (zf_owner) {
+    if (ZF && zf_owner) {
 #pragma unroll
         for (int m = 0; m < N; ++m) s_own[m] = v[m];
         xq = s_own[mq];
@@ -84,7 +87,7 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
 
     // S8: final state at the channel's last sample
-    if (zf_owner) {
+    if (ZF && zf_owner) {
 #pragma unroll
         for (int m = 0; m < N; ++m) s_own[m] = v[m];
         const float yq = s_own[mq];
@@ -113,7 +116,7 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
 //     y_{m-s} = v~_{m-s} - c_i y_{m-2s} - d_i y_{m-4s}, indices below 0
 //     taken from the previous lane (S_R) or the one before (S_R^2).
 // Sequential depth log2 N per stage instead of N.
-template <int N, bool FACT>
+template <int N, bool FACT, bool ZF = false>
 __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, const float b0,
                                                 const float4* cr, float& Z1, float& Z2,
                                                 bool zf_owner, int mq, float* s_own,
@@ -128,7 +131,7 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
 
     float xq = 0.f, xqm1 = 0.f;
     __syncwarp();
-    if (zf_owner) {
+    if (ZF && zf_owner) {
 #pragma unroll
         for (int m = 0; m < N; ++m) s_own[m] = v[m];
         xq = s_own[mq];
@@ -215,7 +218,7 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
 
     // S8: final state at the channel's last sample
-    if (zf_owner) {
+    if (ZF && zf_owner) {
         // DF2T z2 entering this lane: b2 x_{-1} - a2 y_{-1}
         const float zin2 = lane == 0 ? zi2 : fmaf(b2, px1, -a2 * Y1);
 #pragma unroll
@@ -230,6 +233,57 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
         zf_dst[1] = f2 * G;
     }
     __syncwarp();
+}
+
+// The group holding the channel's last sample, out of line: the lane chunk
+// travels through the lane's shared-memory row (row[0, N)), so the registers
+// the run-time zf indexing needs are not reserved by the callers' hot loops.
+// coef: Phi^(2^j) (PH) or the cyclic-reduction coefficients (CR).  Returns
+// the group's outgoing state.
+template <int N, bool FACT, bool CR>
+__device__ __noinline__ float2 section_zf_row(float* row, const float4 ab, const float b0,
+                                              const float4* coef, const float4 lp, float2 z,
+                                              bool zf_owner, int mq, float* zf_dst, float G) {
+    float v[N];
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+        v[4 * q + 0] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+    if (CR)
+        pipe_section_cr<N, FACT, true>(v, ab, b0, coef, z.x, z.y, zf_owner, mq, row, zf_dst, G);
+    else
+        pipe_section<N, FACT, true>(v, ab, b0, coef, lp, z.x, z.y, zf_owner, mq, row, zf_dst, G);
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+        *reinterpret_cast<float4*>(row + 4 * q) =
+            make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    __syncwarp();
+    return z;
+}
+
+// Chunk v[] <-> the lane's row, around section_zf_row.
+template <int N>
+__device__ __forceinline__ void chunk_to_row(const float (&v)[N], float* row) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+        *reinterpret_cast<float4*>(row + 4 * q) =
+            make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void row_to_chunk(float (&v)[N], const float* row) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+        v[4 * q + 0] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
 }
 
 }  // namespace sosf

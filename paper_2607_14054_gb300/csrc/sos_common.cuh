@@ -40,7 +40,9 @@ struct WsHeader {
     uint32_t done;          // CTAs of the running filter launch that have finished
     int64_t nrounds;        // interleaved dispatch: rounds (longest channel's tiles); 0 = channel-major
     int64_t total_pipe;     // segments of the section pipeline (channels within their horizon)
-    int64_t pad1[2];
+    unsigned long long seg_next;  // warp-segment kernel: segments handed out past the first round
+    uint32_t seg_done;      // warp-segment kernel: warps of the running launch that have finished
+    uint32_t pad1;
 };
 static_assert(sizeof(WsHeader) == 64, "header size");
 

@@ -55,24 +55,11 @@ struct PipeShared {
     float4 cr[kMaxSections][14];                     // section k's cyclic-reduction coefficients
 };
 
-// try_wait with a suspend-time hint: a warp whose slot is not ready yet
-// sleeps until the phase completes (or the hint runs out) instead of polling.
-__device__ __forceinline__ bool mbar_try_wait_sleep(unsigned long long* b, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(b)), "r"(parity), "r"(1000000u)
-        : "memory");
-    return ok != 0;
-}
-
 // Bounded, warp-uniform wait for an mbarrier phase.
 __device__ __forceinline__ void pipe_wait(const Params& p, unsigned long long* b, unsigned par,
                                           int lane) {
     for (uint32_t it = 0;; ++it) {
-        const bool ok = mbar_try_wait_sleep(b, par);
+        const bool ok = mbar_try_wait(b, par);
         if (__all_sync(0xffffffffu, ok)) return;
         if (it >= kHandOffLimit) {
             if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);

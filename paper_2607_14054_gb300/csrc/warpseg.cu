@@ -1,0 +1,292 @@
+// Warp-segment forward kernel for channels within their memory horizon.
+//
+// The alternative to the section pipeline (pipe.cu) for the same segments:
+// one warp runs all K sections of its own segment, group after group, each
+// section carrying its DF2T state from one group to the next in registers
+// (the paper's group chaining, Sec. V).  A GPU holds a few thousand such
+// independent streams and none waits on another warp: there are no
+// hand-overs and no pipeline fill, at the price of segments short enough to
+// give every warp work, and so a larger share of warm-up (the memory horizon
+// P, run from zero state before every segment but a channel's first).
+//
+// Per warp: two shared-memory slots of one group each (rows padded to N + 4
+// floats).  While the sections run on one group in registers, cp.async fills
+// the other slot with the next group (of this segment, or the first of the
+// warp's next one).  The stride-N permutation in and out is paid once per
+// group for the whole cascade (Sec. VII-B).
+#include "pipe_section.cuh"
+#include "sos_pipe.cuh"
+
+namespace sosf {
+
+constexpr int kWsWarps = 4;  // warps per CTA
+constexpr int kWsThreads = kWsWarps * 32;
+
+// CTAs per SM the register budget is sized for (shared memory allows as many)
+template <int N>
+constexpr int ws_ctas_per_sm() {
+    return N == 16 ? 4 : N == 32 ? 3 : 2;
+}
+
+template <int N>
+struct WsCfg {
+    static constexpr int kGroup = 32 * N;
+    static constexpr int kGran = kGroup / 4;
+    static constexpr int kSlot = 32 * (N + 4);  // floats per slot
+    static constexpr size_t kSmem = sizeof(float) * kSlot * 2 * kWsWarps;
+};
+
+// the asynchronous copies of one group (rem samples left in the channel)
+template <int N>
+__device__ __forceinline__ void ws_load(const float* src, int64_t rem, float* slot, int lane) {
+    using SL = SlotLayout<N>;
+    using WC = WsCfg<N>;
+    if (rem >= WC::kGroup && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
+        const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+        for (int q = 0; q < WC::kGran / 32; ++q)
+            cp_async16(slot + SL::gran(q * 32 + lane), s4 + q * 32 + lane);
+    } else {
+        const int r = (int)(rem < WC::kGroup ? rem : WC::kGroup);
+        for (int j = lane; j < WC::kGroup; j += 32)
+            cp_async4(slot + SL::elem(j), j < r ? src + j : src, j < r);
+    }
+    cp_async_commit();
+}
+
+// All groups of one segment through all K sections (one warp).  On entry
+// slot `cur` holds the segment's first group if `pending`; on exit `cur` is
+// the slot of the next segment's first group, and `pending` says whether it
+// was issued (nsrc: that group's source, nullptr if none).
+template <int N, bool FACT, bool CR>
+__device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, float* slots,
+                                           float2* zs, int lane, int& cur, bool& pending,
+                                           const float* nsrc, int64_t nrem) {
+    using SL = SlotLayout<N>;
+    using WC = WsCfg<N>;
+    const int K = sg.K;
+    const Coef32* cf0 = p.c32 + (int64_t)sg.c * p.kmax;
+    // the state entering the segment (zs[k], the same in every lane): zi
+    // (scaled by 1/G_k when b0 is factored) on the channel's first segment,
+    // zero state after a warm-up
+    __syncwarp();
+    if (lane < K) {
+        float2 z = make_float2(0.f, 0.f);
+        if (sg.si == 0 && p.zi) {
+            const float gi = FACT ? __ldg(&cf0[lane].misc.z) : 1.f;
+            z.x = __ldg(p.zi + ((int64_t)sg.c * p.kmax + lane) * 2 + 0) * gi;
+            z.y = __ldg(p.zi + ((int64_t)sg.c * p.kmax + lane) * 2 + 1) * gi;
+        }
+        zs[lane] = z;
+    }
+    __syncwarp();
+    // the group holding the channel's last sample (zf), if in this segment
+    int g_last = -1, owner = 0, mq = 0;
+    if (p.zf && sg.out_hi == sg.len) {
+        const int rel = (int)(sg.len - 1 - sg.cstart);
+        g_last = rel / WC::kGroup;
+        owner = (rel % WC::kGroup) / N;
+        mq = rel % N;
+    }
+    const float Gk = FACT ? __ldg(&cf0[K - 1].misc.y) : 1.f;
+    const float* src0 = p.x + sg.off + sg.cstart;
+    float* dst0 = p.y + sg.off + sg.cstart;
+    const int64_t rem0 = sg.len - sg.cstart;
+    if (!pending) ws_load<N>(src0, rem0, slots + cur * WC::kSlot, lane);
+    pending = false;
+    for (int g = 0; g < sg.ngroups; ++g) {
+        // prefetch: the segment's next group, or the next segment's first
+        float* nxt = slots + (cur ^ 1) * WC::kSlot;
+        if (g + 1 < sg.ngroups) {
+            const int64_t o = (int64_t)(g + 1) * WC::kGroup;
+            ws_load<N>(src0 + o, rem0 - o, nxt, lane);
+            cp_async_wait1();
+        } else if (nsrc) {
+            ws_load<N>(nsrc, nrem, nxt, lane);
+            pending = true;
+            cp_async_wait1();
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+        }
+        __syncwarp();
+        float* slot = slots + cur * WC::kSlot;
+        float* row = slot + lane * SL::kRow;
+        float v[N];
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+            v[4 * q + 0] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
+        }
+        const bool zf_owner = g == g_last && lane == owner;
+        // one copy of the section code (a rolled loop keeps the kernel's
+        // instruction footprint inside the instruction cache)
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            {
+                // plain (L1-cached) loads at the point of use: read-only
+                // loads would be hoisted out of the group loop, eight
+                // sections' worth of live registers
+                const Coef32* cf = cf0 + k;
+                const float4 ab = cf->ab;
+                const float b0 = FACT ? 1.f : cf->misc.x;
+                const float G = FACT ? cf->misc.y : 1.f;
+                float* zf_dst = p.zf + ((int64_t)sg.c * p.kmax + k) * 2;
+                float2 z = zs[k];
+                if (g == g_last) {
+                    const float4 lp = CR ? ab : cf->lane_pow[lane];
+                    chunk_to_row<N>(v, row);
+                    z = section_zf_row<N, FACT, CR>(row, ab, b0, CR ? &cf->cr_lv[0] : cf->phi_pow,
+                                                    lp, z, zf_owner, mq, zf_dst, G);
+                    row_to_chunk<N>(v, row);
+                } else if (CR) {
+                    pipe_section_cr<N, FACT, false>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, false, 0,
+                                                    row, zf_dst, G);
+                } else {
+                    const float4 lp = cf->lane_pow[lane];
+                    pipe_section<N, FACT, false>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, false, 0,
+                                                 row, zf_dst, G);
+                }
+                // every lane holds the outgoing state; the writes agree
+                if (lane == 0) zs[k] = z;
+            }
+        }
+        if (FACT) {
+#pragma unroll
+            for (int m = 0; m < N; ++m) v[m] *= Gk;
+        }
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            *reinterpret_cast<float4*>(row + 4 * q) =
+                make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        __syncwarp();
+        // coalesced stores of the segment's own samples of this group
+        const int64_t gs = (int64_t)g * WC::kGroup;
+        const int64_t a = sg.out_lo - sg.cstart - gs, b = sg.out_hi - sg.cstart - gs;
+        const int lo = (int)(a > 0 ? a : 0), hi = (int)(b < WC::kGroup ? b : WC::kGroup);
+        float* dst = dst0 + gs;
+        const bool aligned = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
+        if (lo == 0 && hi == WC::kGroup && aligned) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+#pragma unroll
+            for (int q = 0; q < WC::kGran / 32; ++q)
+                __stcs(d4 + q * 32 + lane,
+                       *reinterpret_cast<const float4*>(slot + SL::gran(q * 32 + lane)));
+        } else if (((lo | hi) & 3) == 0 && aligned) {
+            float4* d4 = reinterpret_cast<float4*>(dst);
+            for (int q = (lo >> 2) + lane; q < (hi >> 2); q += 32)
+                __stcs(d4 + q, *reinterpret_cast<const float4*>(slot + SL::gran(q)));
+        } else {
+            for (int j = lo + lane; j < hi; j += 32) __stcs(dst + j, slot[SL::elem(j)]);
+        }
+        __syncwarp();
+        cur ^= 1;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_kernel(Params p) {
+    using WC = WsCfg<N>;
+    extern __shared__ float4 s_ws4[];
+    __shared__ float2 s_z[kWsWarps][kMaxSections];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    float* slots = reinterpret_cast<float*>(s_ws4) + (size_t)w * 2 * WC::kSlot;
+    const int64_t total = p.hdr->total_pipe;  // segments of the latest plan
+    const int64_t nw = (int64_t)gridDim.x * kWsWarps;
+    int cur = 0;
+    bool pending = false;
+    // segments: the first nw one per warp, the rest handed out in order as
+    // warps come free (segments differ in length across uneven channels)
+    int64_t d = (int64_t)blockIdx.x * kWsWarps + w;
+    SegGeom sg{};
+    if (d < total) sg = seg_geom<WC::kGroup>(p, d);
+    while (d < total) {
+        // the warp's next segment, taken one ahead for the prefetch (only its
+        // first group's source is kept live; its geometry is looked up again)
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(&p.hdr->seg_next, 1ull);
+        const int64_t dn = nw + (int64_t)__shfl_sync(0xffffffffu, t, 0);
+        const float* nsrc = nullptr;
+        int64_t nrem = 0;
+        if (dn < total) {
+            const SegGeom nx = seg_geom<WC::kGroup>(p, dn);
+            if (nx.K > 0) {
+                nsrc = p.x + nx.off + nx.cstart;
+                nrem = nx.len - nx.cstart;
+            }
+        }
+        if (sg.K == 0) {
+            // identity channel: copy the segment's own samples
+            for (int64_t i = sg.out_lo + lane; i < sg.out_hi; i += 32)
+                p.y[sg.off + i] = __ldg(p.x + sg.off + i);
+        } else {
+            const bool fact = p.chan[sg.c].mode != 0;
+            // cyclic reduction when the call asks for it and every section of
+            // the channel is well conditioned for it, PH otherwise
+            bool cr = p.algo == 2;
+            for (int k = 0; k < sg.K && cr; ++k)
+                cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
+            if (fact && cr)
+                ws_segment<N, true, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+            else if (fact)
+                ws_segment<N, true, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+            else if (cr)
+                ws_segment<N, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+            else
+                ws_segment<N, false, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+        }
+        d = dn;
+        if (d < total) sg = seg_geom<WC::kGroup>(p, d);
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    // the last warp to finish resets the hand-out for the next launch (every
+    // warp's last atomicAdd on seg_next precedes its arrival here)
+    if (lane == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(&p.hdr->seg_done, 1u);
+        if (prev + 1 == (unsigned)nw) {
+            p.hdr->seg_next = 0;
+            p.hdr->seg_done = 0;
+            __threadfence();
+        }
+    }
+}
+
+#define SOSF_WS(N_) reinterpret_cast<const void*>(&sos_warpseg_kernel<N_>)
+
+namespace {
+const void* ws_fn(int N) { return N == 16 ? SOSF_WS(16) : N == 32 ? SOSF_WS(32) : SOSF_WS(64); }
+size_t ws_smem(int N) { return sizeof(float) * 32 * (size_t)(N + 4) * 2 * kWsWarps; }
+}  // namespace
+
+// CTAs of the warp-segment kernel resident per SM (0 on error)
+int warpseg_ctas_per_sm(int N) {
+    static int s_occ[3] = {0, 0, 0};
+    const int idx = N == 16 ? 0 : N == 32 ? 1 : 2;
+    if (s_occ[idx] == 0) {
+        const void* fn = ws_fn(N);
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ws_smem(N)) != cudaSuccess)
+            return 0;
+        int occ = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kWsThreads, ws_smem(N)) !=
+            cudaSuccess)
+            return 0;
+        s_occ[idx] = occ;
+    }
+    return s_occ[idx];
+}
+
+int warpseg_warps_per_cta() { return kWsWarps; }
+
+cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream) {
+    if (warpseg_ctas_per_sm(p.N) < 1) return cudaErrorInvalidConfiguration;
+    if (grid < 1) return cudaSuccess;
+    void* args[] = {const_cast<Params*>(&p)};
+    return cudaLaunchKernel(ws_fn(p.N), dim3((unsigned)grid), dim3(kWsThreads), args, ws_smem(p.N),
+                            stream);
+}
+
+}  // namespace sosf

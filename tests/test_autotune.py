@@ -18,11 +18,12 @@ def test_shape_key_buckets():
 
 def test_candidates():
     h = at.candidates(False)
-    assert len(h) == 6 and {c[0] for c in h} == {16, 32, 64} and {c[2] for c in h} == {1, 2}
+    assert len(h) == 12 and {c[0] for c in h} == {16, 32, 64} and {c[2] for c in h} == {1, 2}
+    assert {c[3] for c in h} == {0, 4}  # section pipeline and warp segments
     c = at.candidates(True)
     assert set(c) >= set(h)
     assert all((n, w) in at.SUPPORTED_NW for (n, w, _, _) in c)
-    assert len(c) == 2 * len(at.SUPPORTED_NW)
+    assert len(c) == 4 * len(at.SUPPORTED_NW)
 
 
 def test_cache_file_round_trip(tmp_path, monkeypatch):
