@@ -91,6 +91,11 @@ typedef enum sos_status {
  *             every resident warp work).  Segment lengths differ, so the same
  *             flags must reach sos_prepare and sos_apply.  The backward always
  *             runs the section pipeline.
+ *             bits 8..11 (SOS_FLAG_WS_CTAS(n)): CTAs per SM of the
+ *             warp-segment launch, 1..15 (0 = as many as fit; more than fit
+ *             is clamped).  Fewer, longer-running warps suit calls whose
+ *             segments fill the GPU about once (one long signal); the most
+ *             that fit suit large batches.
  *
  * Cross-tile state.  The plan bounds each channel's impulse-response tail by
  * partial fractions over its poles and finds its memory horizon P: the warm-up
@@ -111,6 +116,7 @@ typedef struct sos_tuning {
 #define SOS_FLAG_CHECK_STABLE 1
 #define SOS_FLAG_CARRY_ONLY 2
 #define SOS_FLAG_SECTION_PIPELINE 4
+#define SOS_FLAG_WS_CTAS(n) (((n) & 15) << 8)
 #define SOS_MAX_SECTIONS 8
 
 /* Bytes of device workspace needed for a call with these sizes.

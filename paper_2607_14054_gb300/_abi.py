@@ -20,6 +20,12 @@ SOS_OK = 0
 SOS_FLAG_CHECK_STABLE = 1
 SOS_FLAG_CARRY_ONLY = 2
 SOS_FLAG_SECTION_PIPELINE = 4
+
+
+def SOS_FLAG_WS_CTAS(n: int) -> int:  # noqa: N802 - the C macro's name
+    return (int(n) & 15) << 8
+
+
 SOS_MAX_SECTIONS = 8
 
 STATUS_NAMES = {

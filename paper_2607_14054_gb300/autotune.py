@@ -42,20 +42,33 @@ def shape_key(lengths: Sequence[int], kmax: int, carried: bool) -> Tuple:
     return (int(kmax), lb, cb, "carried" if carried else "horizon")
 
 
-KERNELS = (0, 4)  # warp segments, section pipeline (SOS_FLAG_SECTION_PIPELINE)
+SECTION_PIPELINE = 4  # SOS_FLAG_SECTION_PIPELINE
+
+
+def ws_ctas(n: int) -> int:
+    """SOS_FLAG_WS_CTAS(n): CTAs per SM of the warp-segment launch."""
+    return (n & 15) << 8
+
+
+# flags for the channels within their memory horizon: the warp-segment kernel
+# at the most CTAs per SM that fit and at fewer (longer-running warps, for
+# calls whose segments fill the GPU about once), and the section pipeline
+KERNELS = {16: (0, ws_ctas(3), SECTION_PIPELINE),
+           32: (0, ws_ctas(3), ws_ctas(2), SECTION_PIPELINE),
+           64: (0, ws_ctas(2), SECTION_PIPELINE)}
 
 
 def candidates(carried: bool) -> List[Tuple[int, int, int, int]]:
-    """Tunings to try: every N with both solvers and both kernels for the
-    channels within their memory horizon; several W only when some channel
-    is carried by the look-back (W sizes the look-back tiles)."""
+    """Tunings to try: every N with both solvers and each kernel choice for
+    the channels within their memory horizon; several W only when some
+    channel is carried by the look-back (W sizes the look-back tiles)."""
     out = []
     for n in (16, 32, 64):
         ws = sorted({w for (nn, w) in SUPPORTED_NW if nn == n}) if carried else \
             [8 if (n, 8) in SUPPORTED_NW else min(w for (nn, w) in SUPPORTED_NW if nn == n)]
         for w in ws:
             for a in ALGOS:
-                for f in KERNELS:
+                for f in KERNELS[n]:
                     out.append((n, w, a, f))
     return out
 

@@ -12,7 +12,7 @@ cudaError_t launch_adjoint(const Params& p, int64_t grid, double* grad_sos, cuda
 bool forward_supported(int N, int W);
 bool pipe_supported(int N);
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream);
-int warpseg_ctas_per_sm(int N);
+int warpseg_ctas_per_sm(int N, int algo);
 int warpseg_warps_per_cta();
 }  // namespace sosf
 
@@ -59,12 +59,20 @@ constexpr int kPipeCtasPerSm = 2;
 // the warp-segment kernel, each resident warp (at least 8192 samples, so that
 // horizons up to 4096 samples qualify as with the pipeline, and at most 64
 // groups).
-int64_t segment_length(int64_t total_len, int N, bool warp_segments) {
+// CTAs per SM of a warp-segment launch: the tuning's request (flag bits
+// 8..11), at most as many as fit; 0 = as many as fit.
+int warpseg_ctas(int N, int algo, int flags) {
+    const int fit = warpseg_ctas_per_sm(N, algo);
+    const int req = (flags >> 8) & 15;
+    return req > 0 && req < fit ? req : fit;
+}
+
+int64_t segment_length(int64_t total_len, int N, int algo, int flags, bool warp_segments) {
     const int64_t group = 32LL * N;
     const int sms = device_sms() > 0 ? device_sms() : 148;
     int64_t units = (int64_t)sms * kPipeCtasPerSm, gmin = 8;
     if (warp_segments) {
-        const int occ = warpseg_ctas_per_sm(N);
+        const int occ = warpseg_ctas(N, algo, flags);
         units = (int64_t)sms * (occ > 0 ? occ : 1) * warpseg_warps_per_cta();
         gmin = (8192 + group - 1) / group;
     }
@@ -164,7 +172,8 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->W = tu.W;
     p->flags_opt = tu.flags;
     p->algo = tu.algo;
-    p->seg = segment_length(total_len, tu.N, (tu.flags & SOS_FLAG_SECTION_PIPELINE) == 0);
+    p->seg = segment_length(total_len, tu.N, tu.algo, tu.flags,
+                            (tu.flags & SOS_FLAG_SECTION_PIPELINE) == 0);
     p->total = total_len;
     *tiles_out = tiles;
     *total_len_out = total_len;
@@ -227,7 +236,8 @@ sos_status apply_parts(const float* x, int32_t n_channels, int32_t kmax,
         if (p.flags_opt & SOS_FLAG_SECTION_PIPELINE)
             e = launch_pipe(p, sms * kPipeCtasPerSm, static_cast<cudaStream_t>(stream));
         else
-            e = launch_warpseg(p, sms * warpseg_ctas_per_sm(p.N), static_cast<cudaStream_t>(stream));
+            e = launch_warpseg(p, sms * warpseg_ctas(p.N, p.algo, p.flags_opt),
+                               static_cast<cudaStream_t>(stream));
         if (e != cudaSuccess) return SOS_ERR_CUDA;
     }
     if (parts & kPartCarry) {
@@ -406,7 +416,7 @@ sos_status sos_filter_backward(const float* x, const double* sos, const int32_t*
     p.lengths = lengths;
     // the backward runs the section pipeline, on its segment length
     p.flags_opt |= kFlagBackwardPlan | SOS_FLAG_SECTION_PIPELINE;
-    p.seg = segment_length(total, p.N, false);
+    p.seg = segment_length(total, p.N, p.algo, p.flags_opt, false);
     p.inter = reinterpret_cast<float*>(ws + BL.inter);
     p.gacc = reinterpret_cast<double*>(ws + BL.gacc);
     if (launch_plan(p, sm) != cudaSuccess) return SOS_ERR_CUDA;

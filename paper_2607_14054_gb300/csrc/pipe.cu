@@ -29,8 +29,9 @@
 
 namespace sosf {
 
-// The groups of one segment through section k (warp 1 + k).
-template <int N, bool FACT, bool CR>
+// The groups of one segment through section k (warp 1 + k).  ZFK: the call
+// asks for final states (the zf instantiation of the section is compiled in).
+template <int N, bool FACT, bool CR, bool ZFK>
 __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegGeom& sg, int k,
                                                      PipeShared& sh, float* ring, int& s,
                                                      unsigned& use, const float4 ab,
@@ -49,7 +50,7 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
     const bool last_k = k == sg.K - 1;
     // the group holding the channel's last sample (zf), if in this segment
     int g_last = -1, owner = 0, mq = 0;
-    if (p.zf && sg.out_hi == sg.len) {
+    if (ZFK && sg.out_hi == sg.len) {
         const int rel = (int)(sg.len - 1 - sg.cstart);
         g_last = rel / (32 * N);
         owner = (rel % (32 * N)) / N;
@@ -72,8 +73,12 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
                 v[4 * q + 2] = t.z;
                 v[4 * q + 3] = t.w;
             }
-            pipe_section<N, FACT, true>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
-                                        FACT ? G : 1.f);
+            if (ZFK && g == g_last)
+                pipe_section<N, FACT, true>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row,
+                                            zf_dst, FACT ? G : 1.f);
+            else
+                pipe_section<N, FACT, false>(v, ab, misc.x, phi, lp, Z1, Z2, false, 0, row,
+                                             zf_dst, 1.f);
             if (p.inter) {
                 float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
                 const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
@@ -99,8 +104,12 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
                 v[4 * q + 2] = t.z;
                 v[4 * q + 3] = t.w;
             }
-            pipe_section_cr<N, FACT, true>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row,
-                                           zf_dst, FACT ? G : 1.f);
+            if (ZFK && g == g_last)
+                pipe_section_cr<N, FACT, true>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row,
+                                               zf_dst, FACT ? G : 1.f);
+            else
+                pipe_section_cr<N, FACT, false>(v, ab, misc.x, sh.cr[k], Z1, Z2, false, 0, row,
+                                                zf_dst, 1.f);
             if (p.inter) {
                 float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
                 const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
@@ -126,7 +135,7 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
     }
 }
 
-template <int N>
+template <int N, bool ZFK>
 __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     using PC = PipeCfg<N>;
     using SL = SlotLayout<N>;
@@ -234,13 +243,17 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
                 const bool cr = p.algo == 2 && sh.cr[k][13].w != 0.f;
                 const bool fact = p.chan[sg.c].mode != 0;
                 if (fact && cr)
-                    pipe_segment_section<N, true, true>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                    pipe_segment_section<N, true, true, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
+                                                          lp);
                 else if (fact)
-                    pipe_segment_section<N, true, false>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                    pipe_segment_section<N, true, false, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
+                                                          lp);
                 else if (cr)
-                    pipe_segment_section<N, false, true>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                    pipe_segment_section<N, false, true, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
+                                                          lp);
                 else
-                    pipe_segment_section<N, false, false>(p, sg, k, sh, ring, s, use, ab, misc, lp);
+                    pipe_segment_section<N, false, false, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
+                                                          lp);
             } else {
                 // past the channel's K: pass the groups through
                 for (int g = 0; g < sg.ngroups; ++g) {
@@ -256,22 +269,26 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     }
 }
 
-#define SOSF_PIPE(N_) reinterpret_cast<const void*>(&sos_pipe_kernel<N_>)
+#define SOSF_PIPE(N_, Z_) reinterpret_cast<const void*>(&sos_pipe_kernel<N_, Z_>)
 
 bool pipe_supported(int N) { return N == 16 || N == 32 || N == 64; }
 
 int64_t pipe_group(int N) { return 32LL * N; }
 
 cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream) {
-    const void* fn = p.N == 16 ? SOSF_PIPE(16) : p.N == 32 ? SOSF_PIPE(32) : SOSF_PIPE(64);
+    const bool z = p.zf != nullptr;
+    const void* fn = z ? (p.N == 16 ? SOSF_PIPE(16, true) : p.N == 32 ? SOSF_PIPE(32, true)
+                                                               : SOSF_PIPE(64, true))
+                       : (p.N == 16 ? SOSF_PIPE(16, false) : p.N == 32 ? SOSF_PIPE(32, false)
+                                                                : SOSF_PIPE(64, false));
     const size_t smem = sizeof(float) * 32 * (size_t)(p.N + 4) * kPipeRing;
-    static bool attr[3] = {false, false, false};
+    static bool attr[2][3] = {{false, false, false}, {false, false, false}};
     const int idx = p.N == 16 ? 0 : p.N == 32 ? 1 : 2;
-    if (!attr[idx]) {
+    if (!attr[z][idx]) {
         const cudaError_t e =
             cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr[idx] = true;
+        attr[z][idx] = true;
     }
     if (grid < 1) return cudaSuccess;
     void* args[] = {const_cast<Params*>(&p)};

@@ -9,12 +9,26 @@
 
 namespace sosf {
 
+// v[mq] and v[mq - 1] (0 when mq = 0) by compile-time-indexed selects, for
+// a run-time mq: no dynamic register indexing, no scratch memory.
+template <int N>
+__device__ __forceinline__ void pick_pair(const float (&v)[N], int mq, float& q0, float& q1) {
+    q0 = v[0];
+    q1 = 0.f;
+#pragma unroll
+    for (int m = 1; m < N; ++m) {
+        q0 = m == mq ? v[m] : q0;
+        q1 = m == mq ? v[m - 1] : q1;
+    }
+}
+
 // One section over one group, lane chunk v[] in registers, from the group's
 // incoming DF2T state (Z1, Z2) (scaled by 1/G_k when b0 is factored); leaves
 // the group's outgoing state in (Z1, Z2).  ZF: the group holds the channel's
-// last sample (at element mq of lane zf_owner's chunk), whose DF2T state goes
-// to zf_dst; a separate instantiation, since the run-time indexing it needs
-// costs registers that every other group would pay for.
+// last sample (at element mq of the chunk of the lane where zf_owner is set),
+// whose DF2T state goes to zf_dst; a separate instantiation, so that other
+// groups do not run the selects it needs.  s_own is unused (kept for the
+// callers' signature).
 template <int N, bool FACT, bool ZF = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
@@ -23,16 +37,10 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     const int lane = threadIdx.x & 31;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
 
-    // S8 support: the section input at the channel's last sample, picked with
-    // a run-time index through the owner's scratch
+    // S8 support: the section input at the channel's last sample (element mq
+    // of the owner's chunk), picked by compile-time-indexed selects
     float xq = 0.f, xqm1 = 0.f;
-    __syncwarp();
-    if (ZF && zf_owner) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s_own[m] = v[m];
-        xq = s_own[mq];
-        xqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
-    }
+    if (ZF) pick_pair<N>(v, mq, xq, xqm1);
 
     // S3: non-recursive stage with zero history inside the lane
     const float xl1 = v[N - 1], xl2 = v[N - 2];
@@ -87,19 +95,18 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
 
     // S8: final state at the channel's last sample
-    if (ZF && zf_owner) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s_own[m] = v[m];
-        const float yq = s_own[mq];
-        const float yqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
+    if (ZF) {
+        float yq, yqm1;
+        pick_pair<N>(v, mq, yq, yqm1);
         float f1;
         if (mq >= 1) f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
         else f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
         const float f2 = fmaf(b2, xq, -a2 * yq);
-        zf_dst[0] = f1 * G;
-        zf_dst[1] = f2 * G;
+        if (zf_owner) {
+            zf_dst[0] = f1 * G;
+            zf_dst[1] = f2 * G;
+        }
     }
-    __syncwarp();
 }
 
 // The same section solved by cyclic reduction (Sec. VI-C) instead of PH.
@@ -130,13 +137,7 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
     const float zi1 = Z1, zi2 = Z2;
 
     float xq = 0.f, xqm1 = 0.f;
-    __syncwarp();
-    if (ZF && zf_owner) {
-#pragma unroll
-        for (int m = 0; m < N; ++m) s_own[m] = v[m];
-        xq = s_own[mq];
-        xqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
-    }
+    if (ZF) pick_pair<N>(v, mq, xq, xqm1);
 
     // S3 with the true history: the previous lane's last two inputs (lane 0's
     // history is inside the group state)
@@ -218,21 +219,20 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
 
     // S8: final state at the channel's last sample
-    if (ZF && zf_owner) {
+    if (ZF) {
         // DF2T z2 entering this lane: b2 x_{-1} - a2 y_{-1}
         const float zin2 = lane == 0 ? zi2 : fmaf(b2, px1, -a2 * Y1);
-#pragma unroll
-        for (int m = 0; m < N; ++m) s_own[m] = v[m];
-        const float yq = s_own[mq];
-        const float yqm1 = mq >= 1 ? s_own[mq - 1] : 0.f;
+        float yq, yqm1;
+        pick_pair<N>(v, mq, yq, yqm1);
         float f1;
         if (mq >= 1) f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
         else f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
         const float f2 = fmaf(b2, xq, -a2 * yq);
-        zf_dst[0] = f1 * G;
-        zf_dst[1] = f2 * G;
+        if (zf_owner) {
+            zf_dst[0] = f1 * G;
+            zf_dst[1] = f2 * G;
+        }
     }
-    __syncwarp();
 }
 
 // The group holding the channel's last sample, out of line: the lane chunk

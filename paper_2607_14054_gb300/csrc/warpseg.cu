@@ -25,7 +25,7 @@ constexpr int kWsThreads = kWsWarps * 32;
 // CTAs per SM the register budget is sized for (shared memory allows as many)
 template <int N>
 constexpr int ws_ctas_per_sm() {
-    return N == 16 ? 4 : N == 32 ? 3 : 2;
+    return N == 16 ? 4 : N == 32 ? 4 : 3;
 }
 
 template <int N>
@@ -54,6 +54,100 @@ __device__ __forceinline__ void ws_load(const float* src, int64_t rem, float* sl
     cp_async_commit();
 }
 
+// Running state of one warp through the groups of its segment.
+struct WsCursor {
+    const float* src;  // the current group's first input sample
+    float* dst;        // its first output sample
+    int rem;           // samples of the channel from src on (capped)
+    int a, b;          // the segment's own outputs, relative to the group start
+};
+
+// One group of a segment through all K sections: prefetch the next group,
+// filter this one in registers, store the segment's own outputs.  ZF: the
+// group holding the channel's last sample, whose final state (zf) is taken at
+// element mq of lane `owner`'s chunk; instantiated apart so that the hot
+// loop holds no zf code.
+template <int N, bool FACT, bool CR, bool ZF>
+__device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, float* slots,
+                                         float2* zs, int lane, int& cur, WsCursor& q, bool last,
+                                         bool& pending, const float* nsrc, int64_t nrem,
+                                         int owner, int mq) {
+    using SL = SlotLayout<N>;
+    using WC = WsCfg<N>;
+    const int K = sg.K;
+    const Coef32* cf0 = p.c32 + (int64_t)sg.c * p.kmax;
+    // prefetch: the segment's next group, or the next segment's first
+    float* nxt = slots + (cur ^ 1) * WC::kSlot;
+    if (!last) {
+        ws_load<N>(q.src + WC::kGroup, q.rem - WC::kGroup, nxt, lane);
+        cp_async_wait1();
+    } else if (nsrc) {
+        ws_load<N>(nsrc, nrem, nxt, lane);
+        pending = true;
+        cp_async_wait1();
+    } else {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    __syncwarp();
+    float* slot = slots + cur * WC::kSlot;
+    float* row = slot + lane * SL::kRow;
+    float v[N];
+    row_to_chunk<N>(v, row);
+    // one copy of the section code (a rolled loop keeps the kernel's
+    // instruction footprint inside the instruction cache); plain (L1-cached)
+    // loads at the point of use: read-only loads would be hoisted out of the
+    // group loop, eight sections' worth of live registers
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const Coef32* cf = cf0 + k;
+        const float4 ab = cf->ab;
+        const float b0 = FACT ? 1.f : cf->misc.x;
+        const float G = (ZF && FACT) ? cf->misc.y : 1.f;
+        float* zf_dst = ZF ? p.zf + ((int64_t)sg.c * p.kmax + k) * 2 : nullptr;
+        float2 z = zs[k];
+        if (CR) {
+            pipe_section_cr<N, FACT, ZF>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, lane == owner, mq,
+                                         row, zf_dst, G);
+        } else {
+            const float4 lp = cf->lane_pow[lane];
+            pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
+                                      row, zf_dst, G);
+        }
+        // every lane holds the outgoing state; the writes agree
+        if (lane == 0) zs[k] = z;
+    }
+    if (FACT) {
+        const float Gk = cf0[K - 1].misc.y;
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[m] *= Gk;
+    }
+    chunk_to_row<N>(v, row);
+    __syncwarp();
+    // coalesced stores of the segment's own samples of this group
+    const int lo = q.a > 0 ? q.a : 0, hi = q.b < WC::kGroup ? q.b : WC::kGroup;
+    const bool aligned = (reinterpret_cast<uintptr_t>(q.dst) & 15u) == 0;
+    if (lo == 0 && hi == WC::kGroup && aligned) {
+        float4* d4 = reinterpret_cast<float4*>(q.dst);
+#pragma unroll
+        for (int i = 0; i < WC::kGran / 32; ++i)
+            __stcs(d4 + i * 32 + lane,
+                   *reinterpret_cast<const float4*>(slot + SL::gran(i * 32 + lane)));
+    } else if (((lo | hi) & 3) == 0 && aligned) {
+        float4* d4 = reinterpret_cast<float4*>(q.dst);
+        for (int i = (lo >> 2) + lane; i < (hi >> 2); i += 32)
+            __stcs(d4 + i, *reinterpret_cast<const float4*>(slot + SL::gran(i)));
+    } else {
+        for (int j = lo + lane; j < hi; j += 32) __stcs(q.dst + j, slot[SL::elem(j)]);
+    }
+    __syncwarp();
+    cur ^= 1;
+    q.src += WC::kGroup;
+    q.dst += WC::kGroup;
+    q.rem -= WC::kGroup;
+    q.a -= WC::kGroup;
+    q.b -= WC::kGroup;
+}
+
 // All groups of one segment through all K sections (one warp).  On entry
 // slot `cur` holds the segment's first group if `pending`; on exit `cur` is
 // the slot of the next segment's first group, and `pending` says whether it
@@ -62,7 +156,6 @@ template <int N, bool FACT, bool CR>
 __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, float* slots,
                                            float2* zs, int lane, int& cur, bool& pending,
                                            const float* nsrc, int64_t nrem) {
-    using SL = SlotLayout<N>;
     using WC = WsCfg<N>;
     const int K = sg.K;
     const Coef32* cf0 = p.c32 + (int64_t)sg.c * p.kmax;
@@ -80,113 +173,32 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
         zs[lane] = z;
     }
     __syncwarp();
-    // the group holding the channel's last sample (zf), if in this segment
-    int g_last = -1, owner = 0, mq = 0;
-    if (p.zf && sg.out_hi == sg.len) {
-        const int rel = (int)(sg.len - 1 - sg.cstart);
-        g_last = rel / WC::kGroup;
-        owner = (rel % WC::kGroup) / N;
-        mq = rel % N;
-    }
-    const float Gk = FACT ? __ldg(&cf0[K - 1].misc.y) : 1.f;
-    const float* src0 = p.x + sg.off + sg.cstart;
-    float* dst0 = p.y + sg.off + sg.cstart;
-    const int64_t rem0 = sg.len - sg.cstart;
-    if (!pending) ws_load<N>(src0, rem0, slots + cur * WC::kSlot, lane);
+    WsCursor q;
+    q.src = p.x + sg.off + sg.cstart;
+    q.dst = p.y + sg.off + sg.cstart;
+    q.rem = (int)(sg.len - sg.cstart < 0x40000000 ? sg.len - sg.cstart : 0x40000000);
+    q.a = (int)(sg.out_lo - sg.cstart);
+    q.b = (int)(sg.out_hi - sg.cstart);
+    if (!pending) ws_load<N>(q.src, q.rem, slots + cur * WC::kSlot, lane);
     pending = false;
-    for (int g = 0; g < sg.ngroups; ++g) {
-        // prefetch: the segment's next group, or the next segment's first
-        float* nxt = slots + (cur ^ 1) * WC::kSlot;
-        if (g + 1 < sg.ngroups) {
-            const int64_t o = (int64_t)(g + 1) * WC::kGroup;
-            ws_load<N>(src0 + o, rem0 - o, nxt, lane);
-            cp_async_wait1();
-        } else if (nsrc) {
-            ws_load<N>(nsrc, nrem, nxt, lane);
-            pending = true;
-            cp_async_wait1();
-        } else {
-            asm volatile("cp.async.wait_all;" ::: "memory");
-        }
-        __syncwarp();
-        float* slot = slots + cur * WC::kSlot;
-        float* row = slot + lane * SL::kRow;
-        float v[N];
-#pragma unroll
-        for (int q = 0; q < N / 4; ++q) {
-            const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
-            v[4 * q + 0] = t.x;
-            v[4 * q + 1] = t.y;
-            v[4 * q + 2] = t.z;
-            v[4 * q + 3] = t.w;
-        }
-        const bool zf_owner = g == g_last && lane == owner;
-        // one copy of the section code (a rolled loop keeps the kernel's
-        // instruction footprint inside the instruction cache)
-#pragma unroll 1
-        for (int k = 0; k < K; ++k) {
-            {
-                // plain (L1-cached) loads at the point of use: read-only
-                // loads would be hoisted out of the group loop, eight
-                // sections' worth of live registers
-                const Coef32* cf = cf0 + k;
-                const float4 ab = cf->ab;
-                const float b0 = FACT ? 1.f : cf->misc.x;
-                const float G = FACT ? cf->misc.y : 1.f;
-                float* zf_dst = p.zf + ((int64_t)sg.c * p.kmax + k) * 2;
-                float2 z = zs[k];
-                if (g == g_last) {
-                    const float4 lp = CR ? ab : cf->lane_pow[lane];
-                    chunk_to_row<N>(v, row);
-                    z = section_zf_row<N, FACT, CR>(row, ab, b0, CR ? &cf->cr_lv[0] : cf->phi_pow,
-                                                    lp, z, zf_owner, mq, zf_dst, G);
-                    row_to_chunk<N>(v, row);
-                } else if (CR) {
-                    pipe_section_cr<N, FACT, false>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, false, 0,
-                                                    row, zf_dst, G);
-                } else {
-                    const float4 lp = cf->lane_pow[lane];
-                    pipe_section<N, FACT, false>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, false, 0,
-                                                 row, zf_dst, G);
-                }
-                // every lane holds the outgoing state; the writes agree
-                if (lane == 0) zs[k] = z;
-            }
-        }
-        if (FACT) {
-#pragma unroll
-            for (int m = 0; m < N; ++m) v[m] *= Gk;
-        }
-#pragma unroll
-        for (int q = 0; q < N / 4; ++q)
-            *reinterpret_cast<float4*>(row + 4 * q) =
-                make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        __syncwarp();
-        // coalesced stores of the segment's own samples of this group
-        const int64_t gs = (int64_t)g * WC::kGroup;
-        const int64_t a = sg.out_lo - sg.cstart - gs, b = sg.out_hi - sg.cstart - gs;
-        const int lo = (int)(a > 0 ? a : 0), hi = (int)(b < WC::kGroup ? b : WC::kGroup);
-        float* dst = dst0 + gs;
-        const bool aligned = (reinterpret_cast<uintptr_t>(dst) & 15u) == 0;
-        if (lo == 0 && hi == WC::kGroup && aligned) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-            for (int q = 0; q < WC::kGran / 32; ++q)
-                __stcs(d4 + q * 32 + lane,
-                       *reinterpret_cast<const float4*>(slot + SL::gran(q * 32 + lane)));
-        } else if (((lo | hi) & 3) == 0 && aligned) {
-            float4* d4 = reinterpret_cast<float4*>(dst);
-            for (int q = (lo >> 2) + lane; q < (hi >> 2); q += 32)
-                __stcs(d4 + q, *reinterpret_cast<const float4*>(slot + SL::gran(q)));
-        } else {
-            for (int j = lo + lane; j < hi; j += 32) __stcs(dst + j, slot[SL::elem(j)]);
-        }
-        __syncwarp();
-        cur ^= 1;
+    // the channel's last sample is in the segment's last group when the
+    // segment ends the channel: that group takes the zf path
+    const int ng = sg.ngroups;
+    const bool zf_last = p.zf && sg.out_hi == sg.len;
+    const int ghot = zf_last ? ng - 1 : ng;
+    for (int g = 0; g < ghot; ++g)
+        ws_group<N, FACT, CR, false>(p, sg, slots, zs, lane, cur, q, g + 1 == ng, pending, nsrc,
+                                     nrem, 0, 0);
+    if (zf_last) {
+        const int rel = (int)(sg.len - 1 - sg.cstart);
+        ws_group<N, FACT, CR, true>(p, sg, slots, zs, lane, cur, q, true, pending, nsrc, nrem,
+                                    (rel % WC::kGroup) / N, rel % N);
     }
 }
 
-template <int N>
+// CRK: the cyclic-reduction instantiation (algo 2).  The PH one carries no
+// cyclic-reduction code, so its register allocation does not pay for it.
+template <int N, bool CRK>
 __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_kernel(Params p) {
     using WC = WsCfg<N>;
     extern __shared__ float4 s_ws4[];
@@ -225,15 +237,15 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
             const bool fact = p.chan[sg.c].mode != 0;
             // cyclic reduction when the call asks for it and every section of
             // the channel is well conditioned for it, PH otherwise
-            bool cr = p.algo == 2;
+            bool cr = CRK;
             for (int k = 0; k < sg.K && cr; ++k)
                 cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
-            if (fact && cr)
-                ws_segment<N, true, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+            if (CRK && fact && cr)
+                ws_segment<N, true, CRK>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+            else if (CRK && cr)
+                ws_segment<N, false, CRK>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
             else if (fact)
                 ws_segment<N, true, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
-            else if (cr)
-                ws_segment<N, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
             else
                 ws_segment<N, false, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
         }
@@ -254,19 +266,23 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
     }
 }
 
-#define SOSF_WS(N_) reinterpret_cast<const void*>(&sos_warpseg_kernel<N_>)
+#define SOSF_WS(N_, CR_) reinterpret_cast<const void*>(&sos_warpseg_kernel<N_, CR_>)
 
 namespace {
-const void* ws_fn(int N) { return N == 16 ? SOSF_WS(16) : N == 32 ? SOSF_WS(32) : SOSF_WS(64); }
+const void* ws_fn(int N, bool cr) {
+    if (cr) return N == 16 ? SOSF_WS(16, true) : N == 32 ? SOSF_WS(32, true) : SOSF_WS(64, true);
+    return N == 16 ? SOSF_WS(16, false) : N == 32 ? SOSF_WS(32, false) : SOSF_WS(64, false);
+}
 size_t ws_smem(int N) { return sizeof(float) * 32 * (size_t)(N + 4) * 2 * kWsWarps; }
 }  // namespace
 
-// CTAs of the warp-segment kernel resident per SM (0 on error)
-int warpseg_ctas_per_sm(int N) {
-    static int s_occ[3] = {0, 0, 0};
-    const int idx = N == 16 ? 0 : N == 32 ? 1 : 2;
-    if (s_occ[idx] == 0) {
-        const void* fn = ws_fn(N);
+// CTAs of the warp-segment kernel (algo 2: the cyclic-reduction one)
+// resident per SM (0 on error)
+int warpseg_ctas_per_sm(int N, int algo) {
+    static int s_occ[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    const int idx = N == 16 ? 0 : N == 32 ? 1 : 2, a = algo == 2 ? 1 : 0;
+    if (s_occ[a][idx] == 0) {
+        const void* fn = ws_fn(N, a == 1);
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ws_smem(N)) != cudaSuccess)
             return 0;
@@ -274,19 +290,19 @@ int warpseg_ctas_per_sm(int N) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kWsThreads, ws_smem(N)) !=
             cudaSuccess)
             return 0;
-        s_occ[idx] = occ;
+        s_occ[a][idx] = occ;
     }
-    return s_occ[idx];
+    return s_occ[a][idx];
 }
 
 int warpseg_warps_per_cta() { return kWsWarps; }
 
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream) {
-    if (warpseg_ctas_per_sm(p.N) < 1) return cudaErrorInvalidConfiguration;
+    if (warpseg_ctas_per_sm(p.N, p.algo) < 1) return cudaErrorInvalidConfiguration;
     if (grid < 1) return cudaSuccess;
     void* args[] = {const_cast<Params*>(&p)};
-    return cudaLaunchKernel(ws_fn(p.N), dim3((unsigned)grid), dim3(kWsThreads), args, ws_smem(p.N),
-                            stream);
+    return cudaLaunchKernel(ws_fn(p.N, p.algo == 2), dim3((unsigned)grid), dim3(kWsThreads), args,
+                            ws_smem(p.N), stream);
 }
 
 }  // namespace sosf

@@ -18,12 +18,16 @@ def test_shape_key_buckets():
 
 def test_candidates():
     h = at.candidates(False)
-    assert len(h) == 12 and {c[0] for c in h} == {16, 32, 64} and {c[2] for c in h} == {1, 2}
-    assert {c[3] for c in h} == {0, 4}  # section pipeline and warp segments
+    assert {c[0] for c in h} == {16, 32, 64} and {c[2] for c in h} == {1, 2}
+    # warp segments at several CTAs per SM and the section pipeline, per N
+    assert len(h) == 2 * sum(len(v) for v in at.KERNELS.values())
+    assert all(4 in {c[3] for c in h if c[0] == n} and 0 in {c[3] for c in h if c[0] == n}
+               for n in (16, 32, 64))
+    assert all(c[3] & ~0xF04 == 0 for c in h)
     c = at.candidates(True)
     assert set(c) >= set(h)
     assert all((n, w) in at.SUPPORTED_NW for (n, w, _, _) in c)
-    assert len(c) == 4 * len(at.SUPPORTED_NW)
+    assert len(c) == 2 * sum(len(at.KERNELS[n]) for (n, _) in at.SUPPORTED_NW)
 
 
 def test_cache_file_round_trip(tmp_path, monkeypatch):

@@ -19,9 +19,10 @@ from test_gpu_forward import _lib, check, random_case, run_gpu, run_oracle
 pytestmark = pytest.mark.gpu
 
 WS, PIPE = 0, 4  # warp segments (default), SOS_FLAG_SECTION_PIPELINE
+WS2 = 2 << 8  # SOS_FLAG_WS_CTAS(2): warp segments, two CTAs per SM
 
 
-@pytest.mark.parametrize("kernel", [WS, PIPE])
+@pytest.mark.parametrize("kernel", [WS, PIPE, WS2])
 @pytest.mark.parametrize("N", [16, 32, 64])
 @pytest.mark.parametrize("algo", [1, 2])
 def test_horizon_kernel_ragged_multichannel(N, algo, kernel):
@@ -109,14 +110,14 @@ def test_warpseg_repeated_calls_identical_and_graph_replay():
     assert plan.device_status() == 0
 
 
-@pytest.mark.parametrize("N,algo", [(32, 1), (16, 2), (64, 1)])
-def test_warpseg_bandpass16_full_size(N, algo):
+@pytest.mark.parametrize("N,algo,flags", [(32, 1, 0), (16, 2, 0), (64, 1, 0), (32, 1, 3 << 8)])
+def test_warpseg_bandpass16_full_size(N, algo, flags):
     wl = workloads.plain_bandpass16(device="cuda")
     args = (wl.x, wl.sos, wl.K, wl.lengths, wl.zi)
-    y, zf = run_gpu(args, tuning=(N, 8, algo, WS))
+    y, zf = run_gpu(args, tuning=(N, 8, algo, flags))
     y_ref, zf_ref = run_oracle(*args)
     err = check(y, zf, y_ref, zf_ref, wl.lengths.numpy(), wl.K.cpu().numpy(), 1e-5)
-    print("bandpass16 warp segments", N, algo, "rel-L2", float(err.max()))
+    print("bandpass16 warp segments", N, algo, flags, "rel-L2", float(err.max()))
 
 
 def test_warpseg_batched_full_size_sampled_channels():
