@@ -6,12 +6,12 @@
 
 namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream);
-cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream);
-cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream);
+cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream, bool early);
+cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream, bool early);
 cudaError_t launch_adjoint(const Params& p, int64_t grid, double* grad_sos, cudaStream_t stream);
 bool forward_supported(int N, int W);
 bool pipe_supported(int N);
-cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream);
+cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early);
 int warpseg_ctas_per_sm(int N, int algo);
 int warpseg_warps_per_cta();
 }  // namespace sosf
@@ -227,23 +227,26 @@ sos_status apply_parts(const float* x, int32_t n_channels, int32_t kmax,
     p.y = y;
     p.zi = zi;
     p.zf = zf;
-    // the warp-segment kernel (or the section pipeline) for channels within
-    // their memory horizon, then the look-back kernel for the others (which also writes the final states
-    // of empty channels and unused sections: at least one CTA)
+    // the warp-segment kernel (or the section pipeline) for the channels
+    // within their memory horizon, then the look-back kernel for the others
+    // (which also writes the final states of empty channels and unused
+    // sections: at least one CTA), launched early so that it starts without a
+    // launch gap once the first has completed
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bool early = false;
     if (total > 0 && (parts & kPartPipe)) {
         const int64_t sms = device_sms() > 0 ? device_sms() : 1;
         cudaError_t e;
         if (p.flags_opt & SOS_FLAG_SECTION_PIPELINE)
-            e = launch_pipe(p, sms * kPipeCtasPerSm, static_cast<cudaStream_t>(stream));
+            e = launch_pipe(p, sms * kPipeCtasPerSm, st, false);
         else
-            e = launch_warpseg(p, sms * warpseg_ctas(p.N, p.algo, p.flags_opt),
-                               static_cast<cudaStream_t>(stream));
+            e = launch_warpseg(p, sms * warpseg_ctas(p.N, p.algo, p.flags_opt), st, false);
         if (e != cudaSuccess) return SOS_ERR_CUDA;
+        early = true;
     }
     if (parts & kPartCarry) {
         const int64_t launch_tiles = tiles > 0 ? tiles : 1;
-        if (launch_forward(p, launch_tiles, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-            return SOS_ERR_CUDA;
+        if (launch_forward(p, launch_tiles, st, early) != cudaSuccess) return SOS_ERR_CUDA;
     }
     return SOS_OK;
 }
@@ -426,7 +429,7 @@ sos_status sos_filter_backward(const float* x, const double* sos, const int32_t*
     p.y = nullptr;
     p.zi = zi;
     p.zf = nullptr;
-    if (total > 0 && launch_pipe(p, grid, sm) != cudaSuccess) return SOS_ERR_CUDA;
+    if (total > 0 && launch_pipe(p, grid, sm, false) != cudaSuccess) return SOS_ERR_CUDA;
     if (cudaMemsetAsync(p.gacc, 0, sizeof(double) * 5 * (size_t)n_channels * kmax, sm) !=
         cudaSuccess)
         return SOS_ERR_CUDA;

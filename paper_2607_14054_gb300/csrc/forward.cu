@@ -380,6 +380,10 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     __shared__ CoefDF s_cdf[kMaxSections];
     int cur_c = -1;
 
+    // launched early behind the horizon kernel (programmatic dependent
+    // launch): the CTAs become resident as that kernel's retire and start
+    // once it has completed, without a launch gap in between
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // Warp 0 coordinates, warps 1..W hold data.  The coordinator is the CTA's
     // oldest warp: its short, latency-bound path is what every data warp
@@ -580,7 +584,8 @@ bool forward_supported(int N, int W) {
     return false;
 }
 
-cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream) {
+cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream,
+                           bool early) {
     const KernelEntry* ke = nullptr;
     for (const auto& e : kEntries)
         if (e.N == p.N && e.W == p.W) ke = &e;
@@ -608,9 +613,7 @@ cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t str
     int64_t grid = (int64_t)s_sms[dev] * s_occ[dev][idx];
     if (host_tiles < grid) grid = host_tiles;
     if (grid < 1) return cudaSuccess;
-    void* args[] = {const_cast<Params*>(&p)};
-    return cudaLaunchKernel(ke->fn, dim3((unsigned)grid), dim3((p.W + 1) * 32), args, ke->smem,
-                            stream);
+    return launch_params(ke->fn, grid, (p.W + 1) * 32, ke->smem, p, stream, early);
 }
 
 }  // namespace sosf

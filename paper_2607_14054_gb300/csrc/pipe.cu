@@ -139,6 +139,9 @@ template <int N, bool ZFK>
 __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     using PC = PipeCfg<N>;
     using SL = SlotLayout<N>;
+    // the look-back kernel queued behind this one may be launched now (it
+    // waits for this kernel's completion before it starts work)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ float4 s_ring4[];
     float* ring = reinterpret_cast<float*>(s_ring4);
     __shared__ PipeShared sh;
@@ -243,17 +246,17 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
                 const bool cr = p.algo == 2 && sh.cr[k][13].w != 0.f;
                 const bool fact = p.chan[sg.c].mode != 0;
                 if (fact && cr)
-                    pipe_segment_section<N, true, true, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
-                                                          lp);
+                    pipe_segment_section<N, true, true, ZFK>(p, sg, k, sh, ring, s, use, ab,
+                                                             misc, lp);
                 else if (fact)
-                    pipe_segment_section<N, true, false, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
-                                                          lp);
+                    pipe_segment_section<N, true, false, ZFK>(p, sg, k, sh, ring, s, use, ab,
+                                                             misc, lp);
                 else if (cr)
-                    pipe_segment_section<N, false, true, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
-                                                          lp);
+                    pipe_segment_section<N, false, true, ZFK>(p, sg, k, sh, ring, s, use, ab,
+                                                             misc, lp);
                 else
-                    pipe_segment_section<N, false, false, ZFK>(p, sg, k, sh, ring, s, use, ab, misc,
-                                                          lp);
+                    pipe_segment_section<N, false, false, ZFK>(p, sg, k, sh, ring, s, use, ab,
+                                                             misc, lp);
             } else {
                 // past the channel's K: pass the groups through
                 for (int g = 0; g < sg.ngroups; ++g) {
@@ -275,7 +278,7 @@ bool pipe_supported(int N) { return N == 16 || N == 32 || N == 64; }
 
 int64_t pipe_group(int N) { return 32LL * N; }
 
-cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream) {
+cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream, bool early) {
     const bool z = p.zf != nullptr;
     const void* fn = z ? (p.N == 16 ? SOSF_PIPE(16, true) : p.N == 32 ? SOSF_PIPE(32, true)
                                                                : SOSF_PIPE(64, true))
@@ -291,8 +294,7 @@ cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream) {
         attr[z][idx] = true;
     }
     if (grid < 1) return cudaSuccess;
-    void* args[] = {const_cast<Params*>(&p)};
-    return cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kPipeThreads), args, smem, stream);
+    return launch_params(fn, grid, kPipeThreads, smem, p, stream, early);
 }
 
 }  // namespace sosf

@@ -4,9 +4,11 @@
 //  * block C (the last one): channel offsets and look-back slots (exclusive
 //    scans of the lengths and of ceil(len / T)) and the status word;
 //  * block c < C: the coefficient tables of channel c, one warp per section,
-//    and (a ninth warp) the channel's memory horizon and tile count;
-//  * order_kernel, after both: the dispatch prefix over the tile counts and,
-//    when some channel carries its state by look-back, the interleaved order.
+//    and two more warps for the b0 factoring and the channel's memory
+//    horizon and tile count;
+//  * the last block to finish (order_pass): the dispatch prefix over the
+//    tile counts and, when some channel carries its state by look-back, the
+//    interleaved order.
 //
 // Coefficient tables (paper Sec. VI-B, "pre-computed before filtering"):
 // the rows are normalised by a0; when every b0 of the channel is nonzero the
@@ -15,7 +17,8 @@
 // The DF2T transition A = [[-a1, 1], [-a2, 0]] is raised to the lane step
 // Phi = A^N, the warp step Psi = A^(NL) and the tile step Theta = A^T by
 // repeated squaring, then the per-lane tables Phi^l, Psi^w and Theta^d by
-// binary powering, each lane forming its own entry.  All of it runs in
+// binary powering, each lane forming its own entry (Psi and Theta only for
+// channels whose state is carried by the look-back).  All of it runs in
 // double-float arithmetic (about 48 significand bits) on the FP32 pipe:
 // GB300's FP64 FMA is 1/64 of its FP32 rate with a 64-cycle latency.  The
 // per-sample tables are rounded once to FP32; the Theta^d used by the
@@ -42,7 +45,7 @@ __device__ __forceinline__ bool finite_row(const double* r) {
     return true;
 }
 
-constexpr int kPlanWarps = kMaxSections + 1;  // one per section + the horizon warp
+constexpr int kPlanWarps = kMaxSections + 2;  // one per section + two horizon warps
 constexpr int kPlanThreads = kPlanWarps * 32;
 
 // complex FP32 helpers for the horizon bound
@@ -58,50 +61,55 @@ __device__ __forceinline__ cpx cdiv(cpx a, cpx b) {
 }
 __device__ __forceinline__ float cabs_(cpx a) { return hypotf(a.re, a.im); }
 
-// Memory horizon of one channel (one warp; rows[k] = normalised b0, b1, b2,
-// a1, a2 of section k).  The cascade's impulse response is, past its first
-// 2K samples, h[n] = sum_i R_i p_i^n over the nonzero poles p_i (partial
-// fractions of prod_k B_k(z) / A_k(z), distinct poles), so its absolute tail
-// from n on is at most sum_i |R_i| |p_i|^n / (1 - |p_i|).  A tile that starts
-// P samples early from zero state drops exactly such a tail of the input's
-// convolution; P is the smallest multiple of 16 (and >= 2K) for which each
-// pole's share is below kHorizonEps * ||h||_2 / (2K), with ||h||_2 bounded
-// from below by half the norm of the first 64 samples (filtered here in
-// FP32).  The initial state's response (DF2T state (k, j) responds with
-// z^-j / A_k(z) * prod_{m > k} B_m / A_m) must likewise have decayed below
-// the bound at the end of the first tile.  Returns -1 when no such P <= T / 2
-// exists, when a pole lies on or outside |z| = 1 - 1e-7, or when two poles
-// are closer than 1e-4 (relative), where the partial fractions are not
-// reliable.
-__device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int lane, cpx* s_pole) {
-    // ||h||_2 lower bound: lane 0 filters a unit impulse for 32 samples
+// Memory horizon of one channel, in two parts run by two warps at once
+// (rows[k] = normalised b0, b1, b2, a1, a2 of section k).  The cascade's
+// impulse response is, past its first 2K samples, h[n] = sum_i R_i p_i^n over
+// the nonzero poles p_i (partial fractions of prod_k B_k(z) / A_k(z), distinct
+// poles), so its absolute tail from n on is at most sum_i |R_i| |p_i|^n /
+// (1 - |p_i|).  A segment that starts P samples early from zero state drops
+// exactly such a tail of the input's convolution; P is the smallest multiple
+// of 16 (and >= 2K) for which each pole's share is below kHorizonEps *
+// ||h||_2 / (2K), with ||h||_2 bounded from below by half the norm of the
+// first 32 samples (horizon_norm, filtered in FP32).  The initial state's
+// response (DF2T state (k, j) responds with z^-j / A_k(z) * prod_{m > k}
+// B_m / A_m) must likewise have decayed below the bound at the end of the
+// first segment.  The horizon is -1 when no such P <= T / 2 exists, when a
+// pole lies on or outside |z| = 1 - 1e-7, or when two poles are closer than
+// 1e-4 (relative), where the partial fractions are not reliable.
+
+// ||h||_2 lower bound: half the norm of the first 32 samples of the impulse
+// response, by a systolic pipeline over the lanes (lane k < K runs section k
+// on sample t - k at step t, taking its input from lane k - 1's previous
+// output).  One warp.
+__device__ float horizon_norm(const float (*rowsf)[5], int K, int lane) {
     float e2 = 0.f;
-    if (lane == 0) {
-        float cb0[kMaxSections], cb1[kMaxSections], cb2[kMaxSections], ca1[kMaxSections],
-            ca2[kMaxSections], z1[kMaxSections], z2[kMaxSections];
-#pragma unroll
-        for (int k = 0; k < kMaxSections; ++k) {
-            const bool on = k < K;
-            cb0[k] = on ? (float)rows[k][0] : 1.f;
-            cb1[k] = on ? (float)rows[k][1] : 0.f;
-            cb2[k] = on ? (float)rows[k][2] : 0.f;
-            ca1[k] = on ? (float)rows[k][3] : 0.f;
-            ca2[k] = on ? (float)rows[k][4] : 0.f;
-            z1[k] = z2[k] = 0.f;
-        }
-        for (int n = 0; n < 32; ++n) {
-            float u = n == 0 ? 1.f : 0.f;
-#pragma unroll
-            for (int k = 0; k < kMaxSections; ++k) {
-                const float y = fmaf(cb0[k], u, z1[k]);
-                z1[k] = fmaf(cb1[k], u, fmaf(-ca1[k], y, z2[k]));
-                z2[k] = fmaf(cb2[k], u, -ca2[k] * y);
-                u = y;
-            }
-            e2 = fmaf(u, u, e2);
+    const bool on = lane < K;
+    const float cb0 = on ? rowsf[lane][0] : 1.f, cb1 = on ? rowsf[lane][1] : 0.f,
+                cb2 = on ? rowsf[lane][2] : 0.f, ca1 = on ? rowsf[lane][3] : 0.f,
+                ca2 = on ? rowsf[lane][4] : 0.f;
+    float z1 = 0.f, z2 = 0.f, y = 0.f;
+    for (int t = 0; t < 32 + K - 1; ++t) {
+        float u = __shfl_up_sync(0xffffffffu, y, 1);
+        if (lane == 0) u = t == 0 ? 1.f : 0.f;
+        const int n = t - lane;
+        if (on && n >= 0 && n < 32) {
+            y = fmaf(cb0, u, z1);
+            z1 = fmaf(cb1, u, fmaf(-ca1, y, z2));
+            z2 = fmaf(cb2, u, -ca2 * y);
+            if (lane == K - 1) e2 = fmaf(y, y, e2);
         }
     }
-    const float h2 = 0.5f * sqrtf(__shfl_sync(0xffffffffu, e2, 0));
+    e2 = K > 0 ? __shfl_sync(0xffffffffu, e2, K - 1) : 1.f;  // K = 0: identity
+    return 0.5f * sqrtf(e2);
+}
+
+// Per-pole terms of the bound that do not depend on ||h||_2 (one warp, lane
+// i < 2K takes pole i): la = log(kHorizonEps (1 - r) / (2K |R_i|)) and
+// ilr = 1 / log r, so that pole i needs P >= (la + log ||h||_2) ilr, and zs =
+// the initial-state response's bound at the end of the first segment.
+// Returns false (for every lane) where the partial fractions are unusable.
+__device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], int K, int64_t T,
+                              int lane, cpx* s_pole, float& la, float& ilr, float& zs) {
     const int np = 2 * K;
     // poles: lane i < 2K takes root (i & 1) of z^2 + a1 z + a2 of section i / 2
     if (lane < np) {
@@ -118,10 +126,11 @@ __device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int la
         s_pole[lane] = z;
     }
     __syncwarp();
-    bool bad = !(h2 > 0.f);
-    float ptail = 0.f, zsum = 0.f;
-    const float budget = kHorizonEps * h2;
-    if (lane < np && !bad) {
+    bool bad = false;
+    la = 0.f;
+    ilr = 0.f;
+    zs = 0.f;
+    if (lane < np) {
         const cpx pi = s_pole[lane];
         const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
         const float r = sqrtf(r2);
@@ -154,36 +163,44 @@ __device__ int channel_horizon(const double (*rows)[5], int K, int64_t T, int la
                                     fmaf(den.re, den.re, den.im * den.im);
                     rz2 = fmaxf(rz2, a * fmaxf(1.f, ir2));
                 }
-                const float b0 = (float)rows[k][0], b1 = (float)rows[k][1], b2 = (float)rows[k][2];
+                const float b0 = rowsf[k][0], b1 = rowsf[k][1], b2 = rowsf[k][2];
                 const cpx Bk{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
                 num = cmul(num, Bk);
             }
             // full cascade: num = prod_m B_m(p_i), den over all other poles
             const float R = sqrtf(fmaf(num.re, num.re, num.im * num.im) /
                                   fmaf(den.re, den.re, den.im * den.im));
-            if (R > 0.f) ptail = logf(budget * (1.f - r) / ((float)np * R)) / logf(r);
-            zsum = sqrtf(rz2) * powf(r, (float)T) / (1.f - r);
-            if (!(ptail < 1e9f) || !(zsum < 1e30f)) bad = true;
+            if (R > 0.f) {
+                la = logf(kHorizonEps * (1.f - r) / ((float)np * R));
+                ilr = 1.f / logf(r);
+            }
+            zs = sqrtf(rz2) * powf(r, (float)T) / (1.f - r);
+            if (!(fabsf(la) < 1e30f) || !(zs < 1e30f)) bad = true;
         }
     }
-    // warp reductions
+    return !__any_sync(0xffffffffu, bad);
+}
+
+// The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp).
+__device__ int horizon_combine(bool ok, float h2, int K, int64_t T, float la, float ilr,
+                               float zs) {
+    float ptail = ilr != 0.f ? (la + logf(h2)) * ilr : 0.f;
+    float zsum = zs;
     for (int o = 16; o > 0; o >>= 1) {
         ptail = fmaxf(ptail, __shfl_xor_sync(0xffffffffu, ptail, o));
         zsum += __shfl_xor_sync(0xffffffffu, zsum, o);
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (bad || !(zsum <= budget)) return -1;
-    const float need = fmaxf(ptail, (float)np);
+    if (!ok || !(h2 > 0.f) || !(ptail < 1e9f) || !(zsum <= kHorizonEps * h2)) return -1;
+    const float need = fmaxf(ptail, (float)(2 * K));
     const int64_t P = ((int64_t)ceilf(need) + 15) / 16 * 16;
     return P <= T / 2 ? (int)P : -1;
 }
 
-// Blocks 0..C-1: coefficients and horizon.  Block C: channel table.
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
+// Block C: the channel table.
+__device__ __forceinline__ void plan_table(const Params& p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int C = p.C, kmax = p.kmax;
-
-    if ((int)blockIdx.x == C) {
+    {
         // ---- channel table: exclusive scans of lengths and slot counts ----
         const int64_t T = (int64_t)p.W * kLanes * p.N;
         __shared__ int64_t s_wsum_len[kPlanWarps], s_wsum_til[kPlanWarps];
@@ -245,64 +262,127 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
             __syncthreads();
         }
         if (tid == 0 && s_carry_til > p.cap_tiles) set_status(p.hdr, SOS_ERR_WORKSPACE);
-        return;
     }
+}
+
+// Block c < C: the coefficient tables and the memory horizon of channel c.
+__device__ __forceinline__ void plan_channel(const Params& p) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int kmax = p.kmax;
 
     // ---- coefficient tables of channel c ----
     // Warps 0..K-1: section k's row, then (lane 0) the squaring chain of its
-    // transition powers and (all lanes) the per-lane tables.  Warp 0 also
-    // decides the b0 factoring.  Warp kMaxSections: the memory horizon.  The
-    // cross-tile tables (powers of Theta) are only built for channels whose
-    // state is carried by the look-back, once the horizon warp has decided.
+    // transition powers and (all lanes) the per-lane tables.  Warp
+    // kMaxSections: the b0 factoring, then the impulse response's norm bound;
+    // warp kMaxSections + 1: the poles' terms of the memory horizon, then the
+    // horizon.  The warp and tile tables (powers of Psi and Theta) are only
+    // built for channels whose state is carried by the look-back, once the
+    // horizon is decided.
     const int c = blockIdx.x;
     __shared__ double s_row[kMaxSections][5];
+    __shared__ float s_rowf[kMaxSections][5];  // the same rows rounded to FP32
     __shared__ double s_G[kMaxSections];
+    __shared__ float s_Ginv[kMaxSections];      // 1 / G_k
+    __shared__ double s_b0inv[kMaxSections];    // 1 / b0 (normalised), 0 if b0 = 0
+    __shared__ float s_h2;                      // ||h||_2 lower bound
     __shared__ int s_mode, s_horizon, s_err;
     __shared__ cpx s_pole[2 * kMaxSections];
     // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
     __shared__ dfm2 s_chain[kMaxSections][20];
 
+    const int k = warp;
+    // the section's row is read before K is known (one memory round trip, not
+    // two): every section k < kmax exists in the sos array
+    double row[6] = {0, 0, 0, 1, 0, 0};
+    if (lane == 0 && k < kmax) {
+        const double* r = p.sos + ((int64_t)c * kmax + k) * 6;
+        for (int i = 0; i < 6; ++i) row[i] = r[i];
+    }
     const int K = p.K[c];
     const int Kc = (K >= 0 && K <= kmax) ? K : 0;
-    const int k = warp;
     const bool active = k < Kc;
     if (tid == 0) s_err = 0;
     __syncthreads();
-    double row[6] = {0, 0, 0, 1, 0, 0};
-    if (active) {
-        const double* r = p.sos + ((int64_t)c * kmax + k) * 6;
-        for (int i = 0; i < 6; ++i) row[i] = r[i];
-        if (!(finite_row(row) && row[3] != 0.0)) {
-            if (lane == 0) atomicCAS(&s_err, 0, (int)SOS_ERR_COEF);
-            row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
-        }
-    }
-    const double ia0 = 1.0 / row[3];
-    const double b0 = row[0] * ia0, b1 = row[1] * ia0, b2 = row[2] * ia0;
-    const double a1 = row[4] * ia0, a2 = row[5] * ia0;
+    // lane 0 of each section warp normalises its row in FP64 (the FP64 unit is
+    // narrow on this part: one lane per row, not the whole warp)
     if (lane == 0 && k < kMaxSections) {
-        s_row[k][0] = b0;
-        s_row[k][1] = b1;
-        s_row[k][2] = b2;
-        s_row[k][3] = a1;
-        s_row[k][4] = a2;
-    }
-    if (active && (p.flags_opt & SOS_FLAG_CHECK_STABLE)) {
+        if (!active) {
+            row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
+        } else {
+            if (!(finite_row(row) && row[3] != 0.0)) {
+                atomicCAS(&s_err, 0, (int)SOS_ERR_COEF);
+                row[0] = 0; row[1] = 0; row[2] = 0; row[3] = 1; row[4] = 0; row[5] = 0;
+            }
+        }
+        const double ia0 = 1.0 / row[3];
+        const double nb0 = row[0] * ia0, nb1 = row[1] * ia0, nb2 = row[2] * ia0;
+        const double na1 = row[4] * ia0, na2 = row[5] * ia0;
+        s_row[k][0] = nb0;
+        s_row[k][1] = nb1;
+        s_row[k][2] = nb2;
+        s_row[k][3] = na1;
+        s_row[k][4] = na2;
+        s_rowf[k][0] = (float)nb0;
+        s_rowf[k][1] = (float)nb1;
+        s_rowf[k][2] = (float)nb2;
+        s_rowf[k][3] = (float)na1;
+        s_rowf[k][4] = (float)na2;
+        s_b0inv[k] = nb0 != 0.0 ? row[3] / row[0] : 0.0;
         // both roots of z^2 + a1 z + a2 strictly inside the unit circle
         // (Jury: |a2| < 1 and |a1| < 1 + a2)
-        if (!(fabs(a2) < 1.0 && fabs(a1) < 1.0 + a2) && lane == 0)
+        if (active && (p.flags_opt & SOS_FLAG_CHECK_STABLE) &&
+            !(fabs(na2) < 1.0 && fabs(na1) < 1.0 + na2))
             atomicCAS(&s_err, 0, (int)SOS_ERR_UNSTABLE);
     }
     __syncthreads();  // rows and errors in shared memory; nothing block-wide after this
+    const int kr = k < kMaxSections ? k : 0;
+    const double b0 = s_row[kr][0], b1 = s_row[kr][1], b2 = s_row[kr][2];
+    const double a1 = s_row[kr][3], a2 = s_row[kr][4];
 
+    const bool carry_only = (p.flags_opt & SOS_FLAG_CARRY_ONLY) != 0;
     if (warp == kMaxSections) {
-        // the horizon warp: memory horizon of channel c (against the
-        // pipeline's segment length) and its work units: pipeline segments
-        // when it has a horizon, look-back tiles otherwise
+        // the first horizon warp.  First the b0 factoring: every b0 nonzero
+        // and 2^-60 < |G_k| < 2^60 for the cumulative gains G_k = b0_1 ...
+        // b0_k (warp prefix product); it releases the section warps (barrier
+        // 1: the Kc section warps and this one), which have been building
+        // their transition powers meanwhile.
+        {
+            const double bj = lane < Kc ? s_row[lane < kMaxSections ? lane : 0][0] : 1.0;
+            double g = bj;
+            for (int d = 1; d < kMaxSections; d <<= 1) {
+                const double t = __shfl_up_sync(0xffffffffu, g, d);
+                if (lane >= d) g *= t;
+            }
+            const bool ok = lane >= Kc || (bj != 0.0 && fabs(g) > 0x1p-60 && fabs(g) < 0x1p60);
+            const int mode = (Kc > 0 && __all_sync(0xffffffffu, ok)) ? 1 : 0;
+            if (lane < kMaxSections) {
+                s_G[lane] = mode ? g : 1.0;
+                s_Ginv[lane] = mode ? 1.f / (float)g : 1.f;
+            }
+            if (lane == 0) {
+                s_mode = mode;
+                p.chan[c].mode = mode;
+                p.chan[c].err = s_err;
+            }
+            if (Kc > 0) asm volatile("bar.arrive 1, %0;" ::"r"(32 * (Kc + 1)) : "memory");
+        }
+        // then the norm bound of the impulse response, for the second
+        // horizon warp (barrier 3: the two horizon warps)
+        const float h2 = carry_only ? 0.f : horizon_norm(s_rowf, Kc, lane);
+        if (lane == 0) s_h2 = h2;
+        asm volatile("bar.arrive 3, 64;" ::: "memory");
+        return;
+    }
+    if (warp == kMaxSections + 1) {
+        // the second horizon warp: the memory horizon of channel c (against
+        // the segment length) and its work units: segments when it has a
+        // horizon, look-back tiles otherwise
         const int64_t T = (int64_t)p.W * kLanes * p.N;
-        int P = (p.flags_opt & SOS_FLAG_CARRY_ONLY)
-                    ? -1
-                    : channel_horizon(s_row, Kc, p.seg, lane, s_pole);
+        float la = 0.f, ilr = 0.f, zs = 0.f;
+        const bool ok = !carry_only &&
+                        horizon_poles(s_row, s_rowf, Kc, p.seg, lane, s_pole, la, ilr, zs);
+        asm volatile("bar.sync 3, 64;" ::: "memory");
+        int P = carry_only ? -1 : horizon_combine(ok, s_h2, Kc, p.seg, la, ilr, zs);
         // backward plans have no look-back: a channel without a horizon is
         // one segment, run from its start to its end by one pipeline
         const int single = (P < 0 && (p.flags_opt & kFlagBackwardPlan)) ? 1 : 0;
@@ -325,97 +405,96 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
         if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
         return;
     }
-    if (warp == 0) {
-        // b0 factoring: every b0 nonzero and 2^-60 < |G_k| < 2^60 for the
-        // cumulative gains G_k = b0_1 ... b0_k (warp prefix product)
-        const double bj = lane < Kc ? s_row[lane < kMaxSections ? lane : 0][0] : 1.0;
-        double g = bj;
-        for (int d = 1; d < kMaxSections; d <<= 1) {
-            const double t = __shfl_up_sync(0xffffffffu, g, d);
-            if (lane >= d) g *= t;
-        }
-        const bool ok = lane >= Kc || (bj != 0.0 && fabs(g) > 0x1p-60 && fabs(g) < 0x1p60);
-        const int mode = (Kc > 0 && __all_sync(0xffffffffu, ok)) ? 1 : 0;
-        if (lane < kMaxSections) s_G[lane] = mode ? g : 1.0;
-        if (lane == 0) {
-            s_mode = mode;
-            p.chan[c].mode = mode;
-            p.chan[c].err = s_err;
-        }
-    }
     if (!active) return;
 
-    // ---- Phi and Psi: double-float squaring chain (lane 0) ----
+    // ---- Phi: double-float squaring chain (lane 0) ----
     const int N = p.N, W = p.W;
     if (lane == 0) {
         const dfm2 A{df_of_double(-a1), df{1.f, 0.f}, df_of_double(-a2), df{0.f, 0.f}};
         dfm2 P = A;
+        // (exact additions: Phi^16 also seeds the look-back's tile powers)
         for (int n = 1; n < N; n <<= 1) P = dfm_mul(P, P);  // A^N (N a power of two)
         s_chain[k][0] = P;
-        for (int j = 1; j < 5; ++j) s_chain[k][j] = dfm_mul(s_chain[k][j - 1], s_chain[k][j - 1]);
-        s_chain[k][5] = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
-        for (int r = 1; r < 5; ++r) s_chain[k][5 + r] = dfm_mul(s_chain[k][4 + r], s_chain[k][4 + r]);
+        for (int j = 1; j < 5; ++j) {
+            P = dfm_mul(P, P);
+            s_chain[k][j] = P;
+        }
     }
-    // cyclic-reduction coefficients in FP64 (lane 1, alongside lane 0's chain)
+    // cyclic-reduction coefficients in double-float (lane 1, alongside lane
+    // 0's chain; about 44 bits, the FP64 unit being narrow on this part)
     if (lane == 1 && p.algo == 2) {
         Coef32* o = p.c32 + ((int64_t)c * kmax + k);
-        double e = a1, f = a2, kappa = 0.0;
+        df e = df_of_double(a1), f = df_of_double(a2);
+        float kappa = 0.f;
         float dd[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         int lv = 0;
         for (int n = 1; n < N; n <<= 1, ++lv) {
-            const double g = f / e;
-            if (e == 0.0 || !isfinite(g)) kappa = INFINITY;
-            else if (fabs(g) > kappa) kappa = fabs(g);
-            o->cr_lv[lv] = make_float4((float)e, (float)f, (float)g, (float)(e - g));
-            dd[lv] = (float)(-f * g);
-            const double e2 = 2.0 * f - e * e;
-            f = f * f;
+            const df g = df_div(f, e);
+            const float gh = df_to_float(g);
+            if (e.hi == 0.f || !(fabsf(gh) < INFINITY)) kappa = INFINITY;
+            else if (fabsf(gh) > kappa) kappa = fabsf(gh);
+            o->cr_lv[lv] = make_float4(df_to_float(e), df_to_float(f), gh,
+                                       df_to_float(df_add(e, df_neg(g))));
+            dd[lv] = -df_to_float(df_mul(f, g));
+            const df e2 = df_add(df_add(f, f), df_neg(df_mul(e, e)));
+            f = df_mul(f, f);
             e = e2;
         }
         o->cr_d[0] = make_float4(dd[0], dd[1], dd[2], dd[3]);
         o->cr_d[1] = make_float4(dd[4], dd[5], dd[6], dd[7]);
         // terminal scan powers C^(2^j), C = [[-e_n, -f_n], [1, 0]], double-float
-        dfm2 C{df_of_double(-e), df_of_double(-f), df{1.f, 0.f}, df{0.f, 0.f}};
+        dfm2 C{df_neg(e), df_neg(f), df{1.f, 0.f}, df{0.f, 0.f}};
         for (int j = 0; j < 5; ++j) {
             o->cr_tpow[j] = to_f4(C);
-            C = dfm_mul(C, C);
+            C = dfm_mul_fast(C, C);
         }
         const bool ok = kappa <= kCrKappaMax;
-        o->cr_misc = make_float4((float)e, (float)f, (float)kappa, ok ? 1.f : 0.f);
+        o->cr_misc = make_float4(df_to_float(e), df_to_float(f), kappa, ok ? 1.f : 0.f);
     }
-    // barrier 1 (the Kc section warps): warp 0's mode and gains are in
-    // shared memory, and this warp's lane 0 has finished its chain
-    asm volatile("bar.sync 1, %0;" ::"r"(32 * Kc) : "memory");
+    // barrier 1 (the Kc section warps and the horizon warp): the mode and
+    // gains are in shared memory, and this warp's lane 0 has finished its
+    // chain
+    asm volatile("bar.sync 1, %0;" ::"r"(32 * (Kc + 1)) : "memory");
     const int mode = s_mode;
 
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
     CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
     {
-        // Phi^lane by binary powering
+        // Phi^lane by binary powering (the cheaper products: rounded to FP32)
         dfm2 P = dfm_identity();
         for (int j = 0; j < 5; ++j)
-            if ((lane >> j) & 1) P = dfm_mul(P, s_chain[k][j]);
+            if ((lane >> j) & 1) P = dfm_mul_fast(P, s_chain[k][j]);
         out32->lane_pow[lane] = to_f4(P);
     }
+    if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);
+    if (lane == 0) {
+        // b1 / b0 and b2 / b0 when b0 is factored (1 / b0 from the rows phase)
+        const double sb = mode ? s_b0inv[k] : 1.0;
+        out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
+        out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], 0.0f);
+        out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
+    }
+
+    // ---- Psi = A^(NL) and Theta = A^T, only for channels carried by the
+    // look-back (its warp and tile steps) ----
+    asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
+    if (s_horizon >= 0) return;
+    if (lane == 0) {
+        dfm2 P = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
+        s_chain[k][5] = P;
+        for (int r = 1; r < 5; ++r) {
+            P = dfm_mul(P, P);
+            s_chain[k][5 + r] = P;
+        }
+    }
+    __syncwarp();
     if (lane < 16) {
         dfm2 P = dfm_identity();
         for (int r = 0; r < 4; ++r)
             if ((lane >> r) & 1) P = dfm_mul(P, s_chain[k][5 + r]);
         out32->psi_w[lane] = to_f4(P);
     }
-    if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);
     if (lane < 4) out32->psi_pow[lane] = to_f4(s_chain[k][5 + lane]);
-    if (lane == 0) {
-        const double sb = mode ? 1.0 / b0 : 1.0;
-        out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
-        const double G = s_G[k];
-        out32->misc = make_float4((float)b0, (float)G, (float)(1.0 / G), 0.0f);
-        out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
-    }
-
-    // ---- Theta = A^T, only for channels carried by the look-back ----
-    asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
-    if (s_horizon >= 0) return;
     if (lane == 0) {
         dfm2 Th = dfm_identity();  // Theta = Psi^W, any W <= 31
         for (int r = 0; r < 5; ++r)
@@ -446,7 +525,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
     }
 }
 
-// Dispatch (one CTA of 1024 threads, runs after plan_kernel).  First the
+// Dispatch (the whole CTA that finishes the plan last).  First the
 // tile prefix tb over the channels' tile counts.  Then, when some channel
 // with more than one tile carries its state by look-back, the interleaved
 // order: tiles are handed out round by round, round r holding tile r of every
@@ -457,8 +536,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
 // round a prefix of that order.  Otherwise (every channel within its memory
 // horizon, or more than kMaxSortChannels channels) nrounds = 0 and tiles go
 // channel by channel, which keeps a tile's overlap with its predecessor in L2.
-__global__ void __launch_bounds__(1024) order_kernel(Params p) {
-    extern __shared__ unsigned long long s_key[];
+__device__ __noinline__ void order_pass(const Params& p, unsigned long long* s_key) {
     const int tid = threadIdx.x, C = p.C;
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ int64_t s_carry;
@@ -477,12 +555,13 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
         const int c = base + tid;
         int64_t nt = 0, ns = 0;
         if (c < C) {
-            const ChanInfo ci = p.chan[c];
-            if (ci.horizon < 0) {
-                nt = ci.ntiles;
+            // written by other blocks of this launch: read past L1
+            const int32_t hz = __ldcg(&p.chan[c].horizon), ntl = __ldcg(&p.chan[c].ntiles);
+            if (hz < 0) {
+                nt = ntl;
                 if (nt > 1) carried = 1;
             } else {
-                ns = ci.ntiles;
+                ns = ntl;
             }
         }
         int64_t inc = nt, inc2 = ns;
@@ -519,7 +598,7 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     const int64_t total = s_carry, total2 = s_carry2;
     const bool interleave = __syncthreads_or(carried) != 0 && C <= kMaxSortChannels;
     if (tid == 0) {
-        const bool bad = p.hdr->status == SOS_ERR_WORKSPACE;
+        const bool bad = __ldcg(&p.hdr->status) == SOS_ERR_WORKSPACE;
         p.tb[C] = total;
         p.tbp[C] = total2;
         p.hdr->total_tiles = bad ? 0 : total;
@@ -533,8 +612,9 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
     for (int i = tid; i < n; i += blockDim.x) {
         // ascending sort of (MAX - ntiles, channel): decreasing tile count,
         // then increasing channel index; padding sorts last
-        const unsigned long long nt =
-            (i < C && p.chan[i].horizon < 0) ? (unsigned long long)p.chan[i].ntiles : 0ull;
+        const unsigned long long nt = (i < C && __ldcg(&p.chan[i].horizon) < 0)
+                                          ? (unsigned long long)__ldcg(&p.chan[i].ntiles)
+                                          : 0ull;
         s_key[i] = i < C ? (((0xffffffffull - nt) << 32) | (unsigned)i) : ~0ull;
     }
     __syncthreads();
@@ -593,21 +673,41 @@ __global__ void __launch_bounds__(1024) order_kernel(Params p) {
 }  // namespace sosf
 
 namespace sosf {
+
+// Blocks 0..C-1: coefficients and horizon of one channel each.  Block C: the
+// channel table.  The last block to finish then builds the dispatch order
+// (order_pass), so that a call's set-up is a single launch.
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
+    extern __shared__ unsigned long long s_key[];
+    __shared__ int s_last;
+    if ((int)blockIdx.x == p.C) plan_table(p);
+    else plan_channel(p);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();  // this block's tables before its arrival
+        const unsigned prev = atomicAdd(&p.hdr->plan_done, 1u);
+        s_last = prev == (unsigned)p.C;  // C + 1 blocks
+        if (s_last) p.hdr->plan_done = 0;  // for the next launch on this workspace
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();  // every block's tables before the order pass reads them
+    order_pass(p, s_key);
+}
+
 cudaError_t launch_plan(const Params& p, cudaStream_t stream) {
-    plan_kernel<<<p.C + 1, kPlanThreads, 0, stream>>>(p);
-    cudaError_t err = cudaGetLastError();
-    if (err != cudaSuccess) return err;
     int n = 1;
     while (n < p.C && n < kMaxSortChannels) n <<= 1;
     const size_t smem = p.C <= kMaxSortChannels ? sizeof(unsigned long long) * (size_t)n : 0;
     static bool attr_set = false;
     if (!attr_set) {
-        err = cudaFuncSetAttribute(order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)(sizeof(unsigned long long) * kMaxSortChannels));
+        const cudaError_t err =
+            cudaFuncSetAttribute(plan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(unsigned long long) * kMaxSortChannels));
         if (err != cudaSuccess) return err;
         attr_set = true;
     }
-    order_kernel<<<1, 1024, smem, stream>>>(p);
+    plan_kernel<<<p.C + 1, kPlanThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 }  // namespace sosf

@@ -34,7 +34,7 @@ struct WsHeader {
     uint32_t epoch;         // bumped by the plan kernel once per call
     uint32_t tile_counter;  // in-order tile dispatch
     int32_t status;         // device-side status of the latest call (sos_status)
-    uint32_t pad0;
+    uint32_t plan_done;     // blocks of the running plan launch that have finished
     int64_t total_tiles;    // tiles of the latest call (device view)
     int32_t nchan;          // channels of the latest call
     uint32_t done;          // CTAs of the running filter launch that have finished
@@ -183,6 +183,26 @@ struct Params {
     double* gacc;        // backward: [C][kmax][5] sums for b0, b1, b2, a1, a2
     int64_t total;       // samples of all channels
 };
+
+// Launch of fn(p); early: programmatic dependent launch, the kernel may be
+// scheduled once the previous kernel in the stream has let it (that kernel
+// executes griddepcontrol.launch_dependents), and waits for that kernel's
+// completion itself (griddepcontrol.wait) before it starts work.
+inline cudaError_t launch_params(const void* fn, int64_t grid, int threads, size_t smem,
+                                 const Params& p, cudaStream_t stream, bool early) {
+    void* args[] = {const_cast<Params*>(&p)};
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = early ? 1 : 0;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
 
 // ---------------------------------------------------------------------------
 // PTX helpers

@@ -71,6 +71,25 @@ __device__ __forceinline__ dfm2 dfm_mul(const dfm2& x, const dfm2& y) {
                 df_add(df_mul(x.c, y.a), df_mul(x.d, y.c)), df_add(df_mul(x.c, y.b), df_mul(x.d, y.d))};
 }
 
+// The same product with the cheaper additions (about 2^-44 relative error per
+// entry): for tables that are rounded to FP32 in the end.
+__device__ __forceinline__ dfm2 dfm_mul_fast(const dfm2& x, const dfm2& y) {
+    return dfm2{df_add_fast(df_mul(x.a, y.a), df_mul(x.b, y.c)),
+                df_add_fast(df_mul(x.a, y.b), df_mul(x.b, y.d)),
+                df_add_fast(df_mul(x.c, y.a), df_mul(x.d, y.c)),
+                df_add_fast(df_mul(x.c, y.b), df_mul(x.d, y.d))};
+}
+
+// a / b: the quotient of the leading parts, corrected once by the remainder
+// a - q1 b (the double-double division of Bailey's DDFUN/QD libraries,
+// reduced to one correction step; about 2^-44 relative error).
+__device__ __forceinline__ df df_div(df a, df b) {
+    const float q1 = a.hi / b.hi;
+    const df r = df_add(a, df_neg(df_mul(df{q1, 0.f}, b)));
+    const float q2 = r.hi / b.hi;
+    return df_fast_two_sum(q1, q2);
+}
+
 __device__ __forceinline__ dfm2 dfm_identity() {
     return dfm2{df{1.f, 0.f}, df{0.f, 0.f}, df{0.f, 0.f}, df{1.f, 0.f}};
 }

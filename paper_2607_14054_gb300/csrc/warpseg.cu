@@ -201,6 +201,9 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
 template <int N, bool CRK>
 __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_kernel(Params p) {
     using WC = WsCfg<N>;
+    // the look-back kernel queued behind this one may be launched now (it
+    // waits for this kernel's completion before it starts work)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ float4 s_ws4[];
     __shared__ float2 s_z[kWsWarps][kMaxSections];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -297,12 +300,11 @@ int warpseg_ctas_per_sm(int N, int algo) {
 
 int warpseg_warps_per_cta() { return kWsWarps; }
 
-cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream) {
+cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early) {
     if (warpseg_ctas_per_sm(p.N, p.algo) < 1) return cudaErrorInvalidConfiguration;
     if (grid < 1) return cudaSuccess;
-    void* args[] = {const_cast<Params*>(&p)};
-    return cudaLaunchKernel(ws_fn(p.N, p.algo == 2), dim3((unsigned)grid), dim3(kWsThreads), args,
-                            ws_smem(p.N), stream);
+    return launch_params(ws_fn(p.N, p.algo == 2), grid, kWsThreads, ws_smem(p.N), p, stream,
+                         early);
 }
 
 }  // namespace sosf
