@@ -8,7 +8,6 @@ namespace sosf {
 cudaError_t launch_plan(const Params& p, cudaStream_t stream);
 cudaError_t launch_forward(const Params& p, int64_t host_tiles, cudaStream_t stream, bool early);
 cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream, bool early);
-cudaError_t launch_adjoint(const Params& p, int64_t grid, double* grad_sos, cudaStream_t stream);
 bool forward_supported(int N, int W);
 bool pipe_supported(int N);
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early);
@@ -366,21 +365,44 @@ sos_status sos_plan_query(void* workspace, int32_t first, int32_t count, int32_t
 // backward
 // ---------------------------------------------------------------------------
 
+namespace sosf {
+cudaError_t launch_adjoint(const Params& p, int sms, double* grad_sos, cudaStream_t stream);
+int64_t adjoint_warps(int N, int sms);
+int64_t adjoint_ck_slots(int N, int64_t total_len, int32_t C);
+}  // namespace sosf
+
 namespace {
 
 struct BwdLayout {
-    size_t inter, gacc, total;
+    size_t ck, gacc, total;
 };
 
-BwdLayout bwd_layout(size_t base, int32_t C, int32_t kmax, int64_t total_len) {
+// the backward's scratch after the forward workspace: forward-state
+// checkpoints of the adjoint kernel and the FP64 coefficient sums
+BwdLayout bwd_layout(size_t base, int32_t C, int32_t kmax, int64_t total_len, int N) {
     BwdLayout L;
     size_t o = align_up(base, 256);
-    L.inter = o;
-    o = align_up(o + sizeof(float) * (size_t)kmax * (size_t)total_len, 256);
+    L.ck = o;
+    o = align_up(o + sizeof(float) * 2 * (size_t)kmax * (size_t)adjoint_ck_slots(N, total_len, C),
+                 256);
     L.gacc = o;
     o = align_up(o + sizeof(double) * 5 * (size_t)C * (size_t)kmax, 256);
     L.total = o;
     return L;
+}
+
+// Backward segment length: the call's samples over the adjoint kernel's
+// resident warps, in whole groups (at least 8, at most 64), so that every
+// warp gets about one segment and a horizon of up to half a segment fits.
+int64_t backward_segment_length(int64_t total_len, int N) {
+    const int64_t group = 32LL * N;
+    const int sms = device_sms() > 0 ? device_sms() : 148;
+    int64_t units = adjoint_warps(N, sms);
+    if (units < 1) units = 1;
+    int64_t g = (total_len + units * group - 1) / (units * group);
+    if (g < 8) g = 8;
+    if (g > 64) g = 64;
+    return g * group;
 }
 
 }  // namespace
@@ -391,9 +413,11 @@ size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64
                                    const sos_tuning* tuning) {
     const size_t base = sos_workspace_size(n_channels, kmax, lengths_host, tuning);
     if (base == 0) return 0;
+    Tune tu;
+    if (!resolve_tuning(tuning, &tu)) return 0;
     int64_t total = 0;
     for (int32_t c = 0; c < n_channels; ++c) total += lengths_host[c];
-    return bwd_layout(base, n_channels, kmax, total).total;
+    return bwd_layout(base, n_channels, kmax, total, tu.N).total;
 }
 
 sos_status sos_filter_backward(const float* x, const double* sos, const int32_t* K,
@@ -410,35 +434,33 @@ sos_status sos_filter_backward(const float* x, const double* sos, const int32_t*
     if (!sos || !K || !lengths || !grad_sos) return SOS_ERR_ARG;
     if (total > 0 && (!x || !grad_y || !grad_x)) return SOS_ERR_ARG;
     const size_t base = ws_layout(n_channels, kmax, tiles).total;
-    const BwdLayout BL = bwd_layout(base, n_channels, kmax, total);
+    const BwdLayout BL = bwd_layout(base, n_channels, kmax, total, p.N);
     if (ws_bytes < BL.total) return SOS_ERR_WORKSPACE;
     char* ws = static_cast<char*>(workspace);
     cudaStream_t sm = static_cast<cudaStream_t>(stream);
     p.sos = sos;
     p.K = K;
     p.lengths = lengths;
-    // the backward runs the section pipeline, on its segment length
-    p.flags_opt |= kFlagBackwardPlan | SOS_FLAG_SECTION_PIPELINE;
-    p.seg = segment_length(total, p.N, p.algo, p.flags_opt, false);
-    p.inter = reinterpret_cast<float*>(ws + BL.inter);
+    // the backward plan: no look-back (a channel without a memory horizon is
+    // one segment), segments sized for the adjoint kernel's warps
+    p.flags_opt |= kFlagBackwardPlan;
+    p.seg = backward_segment_length(total, p.N);
+    p.ck = reinterpret_cast<float*>(ws + BL.ck);
     p.gacc = reinterpret_cast<double*>(ws + BL.gacc);
     if (launch_plan(p, sm) != cudaSuccess) return SOS_ERR_CUDA;
-    const int64_t grid = (int64_t)(device_sms() > 0 ? device_sms() : 1) * kPipeCtasPerSm;
-    // forward pass keeping every section's output
+    if (cudaMemsetAsync(p.gacc, 0, sizeof(double) * 5 * (size_t)n_channels * kmax, sm) !=
+        cudaSuccess)
+        return SOS_ERR_CUDA;
     p.x = x;
     p.y = nullptr;
     p.zi = zi;
     p.zf = nullptr;
-    if (total > 0 && launch_pipe(p, grid, sm, false) != cudaSuccess) return SOS_ERR_CUDA;
-    if (cudaMemsetAsync(p.gacc, 0, sizeof(double) * 5 * (size_t)n_channels * kmax, sm) !=
-        cudaSuccess)
-        return SOS_ERR_CUDA;
-    // adjoint pass and the coefficient gradients
     p.gy = grad_y;
     p.gzf = grad_zf;
     p.gx = grad_x;
     p.gzi = grad_zi;
-    if (launch_adjoint(p, total > 0 ? grid : 0, grad_sos, sm) != cudaSuccess) return SOS_ERR_CUDA;
+    const int sms = device_sms() > 0 ? device_sms() : 1;
+    if (launch_adjoint(p, sms, grad_sos, sm) != cudaSuccess) return SOS_ERR_CUDA;
     return SOS_OK;
 }
 

@@ -62,7 +62,6 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
         pipe_wait(p, &sh.bar[s][k], use & 1u, lane);
         float* row = ring + s * SL::kFloats + lane * SL::kRow;
         const bool zf_owner = g == g_last && lane == owner;
-        const int64_t gs = sg.cstart + (int64_t)g * (32 * N);
         if (!CR) {
             float v[N];
 #pragma unroll
@@ -79,13 +78,6 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
             else
                 pipe_section<N, FACT, false>(v, ab, misc.x, phi, lp, Z1, Z2, false, 0, row,
                                              zf_dst, 1.f);
-            if (p.inter) {
-                float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
-                const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
-#pragma unroll
-                for (int m = 0; m < N; ++m)
-                    if (m >= lo && m < hi) dst[m] = FACT ? v[m] * G : v[m];
-            }
             if (FACT && last_k) {
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] *= G;
@@ -110,13 +102,6 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
             else
                 pipe_section_cr<N, FACT, false>(v, ab, misc.x, sh.cr[k], Z1, Z2, false, 0, row,
                                                 zf_dst, 1.f);
-            if (p.inter) {
-                float* dst = p.inter + (int64_t)k * p.total + sg.off + gs + lane * N;
-                const int64_t lo = sg.out_lo - gs - lane * N, hi = sg.out_hi - gs - lane * N;
-#pragma unroll
-                for (int m = 0; m < N; ++m)
-                    if (m >= lo && m < hi) dst[m] = FACT ? v[m] * G : v[m];
-            }
             if (FACT && last_k) {
 #pragma unroll
                 for (int m = 0; m < N; ++m) v[m] *= G;
@@ -187,8 +172,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kPipeWarps - 1) {
-        // ---- storer (hands the slots back without storing when y is null:
-        // the backward's forward pass keeps only the section outputs) ----
+        // ---- storer ----
         for (int64_t d = blockIdx.x; d < total; d += gridDim.x) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             float* dst = p.y ? p.y + sg.off + sg.cstart : nullptr;

@@ -29,11 +29,16 @@ __device__ __forceinline__ void pick_pair(const float (&v)[N], int mq, float& q0
 // whose DF2T state goes to zf_dst; a separate instantiation, so that other
 // groups do not run the selects it needs.  s_own is unused (kept for the
 // callers' signature).
-template <int N, bool FACT, bool ZF = false>
+// INJ: a DF2T state (zi1, zi2) enters at group-relative sample pinj instead
+// of the group start (the inputs before it being zero): added to the
+// all-pole input at pinj and pinj + 1 (the backward's recompute of a
+// channel's first group, whose grid is anchored elsewhere).
+template <int N, bool FACT, bool ZF = false, bool INJ = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
-                                             float* zf_dst, float G) {
+                                             float* zf_dst, float G, int pinj = -1,
+                                             float zi1 = 0.f, float zi2 = 0.f) {
     const int lane = threadIdx.x & 31;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
 
@@ -49,6 +54,13 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
         v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
     v[1] = fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]);
     if (!FACT) v[0] = b0 * v[0];
+    if (INJ) {
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const int pos = lane * N + m;
+            v[m] += pos == pinj ? zi1 : (pos == pinj + 1 ? zi2 : 0.f);
+        }
+    }
 
     // S4 (i): particular solution from zero state, terminal values only
     float w0 = v[0], w1 = fmaf(-a1, w0, v[1]);
@@ -93,6 +105,9 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     const float o2 = fmaf(b2, xl1, -a2 * v[N - 1]);
     Z1 = __shfl_sync(0xffffffffu, o1, 31);
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
+    // a state injected at the group's last sample: its second component
+    // belongs to the next group
+    if (INJ && pinj == 32 * N - 1) Z1 += zi2;
 
     // S8: final state at the channel's last sample
     if (ZF) {

@@ -175,7 +175,7 @@ struct Params {
     int32_t flags_opt;   // SOS_FLAG_*
     int32_t algo;        // recursive-stage solver: 1 PH, 2 CR where well conditioned
     int64_t seg;         // pipeline segment length (samples, a multiple of 32 N)
-    float* inter;        // [kmax][total] section outputs (backward's forward pass), or null
+    float* ck;           // backward: forward-state checkpoints [slots][kmax][2]
     const float* gy;     // backward: dL/dy [total]
     const float* gzf;    // backward: dL/dzf [C][kmax][2], or null
     float* gx;           // backward: dL/dx [total]
