@@ -296,17 +296,15 @@ __global__ void __launch_bounds__(kBwThreads) sos_adjoint_kernel(Params p) {
                     const float4 br = cf->braw;
                     const float4 lp = cf->lane_pow[lane];
                     float* za = s_za[w][k];
-                    const float4 ab_l = make_float4(ab.x, ab.y, 0.f, 0.f);    // all-pole part
-                    const float4 ab_u = make_float4(ab.x, ab.y, br.y, br.z);  // whole section
                     float zl1 = za[0], zl2 = za[1], zu1 = za[2], zu2 = za[3];
                     const float q1 = za[4], q2 = za[5];
                     float lw[N];
 #pragma unroll
                     for (int m = 0; m < N; ++m) lw[m] = v[m];
-                    pipe_section<N, true>(lw, ab_l, 1.f, cf->phi_pow, lp, zl1, zl2, false, 0,
-                                          nullptr, nullptr, 1.f);
-                    pipe_section<N, false>(v, ab_u, br.x, cf->phi_pow, lp, zu1, zu2, false, 0,
-                                           nullptr, nullptr, 1.f);
+                    // lambda (reversed): all-pole part; dL/du (reversed): the
+                    // whole section; one fused pass
+                    pipe_section_dual<N>(lw, v, ab.x, ab.y, br.x, br.y, br.z, cf->phi_pow, lp,
+                                         zl1, zl2, zu1, zu2);
                     // lambda_{n+1}, lambda_{n+2} of element m are elements m-1,
                     // m-2, the first two from the lane (or group) before
                     float p1 = __shfl_up_sync(0xffffffffu, lw[N - 1], 1);

@@ -33,7 +33,8 @@ __device__ __forceinline__ void pick_pair(const float (&v)[N], int mq, float& q0
 // of the group start (the inputs before it being zero): added to the
 // all-pole input at pinj and pinj + 1 (the backward's recompute of a
 // channel's first group, whose grid is anchored elsewhere).
-template <int N, bool FACT, bool ZF = false, bool INJ = false>
+// NOFIR: the all-pole part alone (b0 = 1, b1 = b2 = 0): S3 is skipped.
+template <int N, bool FACT, bool ZF = false, bool INJ = false, bool NOFIR = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
@@ -48,12 +49,14 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     if (ZF) pick_pair<N>(v, mq, xq, xqm1);
 
     // S3: non-recursive stage with zero history inside the lane
-    const float xl1 = v[N - 1], xl2 = v[N - 2];
+    const float xl1 = NOFIR ? 0.f : v[N - 1], xl2 = NOFIR ? 0.f : v[N - 2];
+    if (!NOFIR) {
 #pragma unroll
-    for (int m = N - 1; m >= 2; --m)
-        v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
-    v[1] = fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]);
-    if (!FACT) v[0] = b0 * v[0];
+        for (int m = N - 1; m >= 2; --m)
+            v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
+        v[1] = fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]);
+        if (!FACT) v[0] = b0 * v[0];
+    }
     if (INJ) {
 #pragma unroll
         for (int m = 0; m < N; ++m) {
@@ -248,6 +251,98 @@ __device__ __forceinline__ void pipe_section_cr(float (&v)[N], const float4 ab, 
             zf_dst[1] = f2 * G;
         }
     }
+}
+
+// The adjoint's two runs of one section on the same reversed input g, fused
+// so that their recursions interleave (two independent chains per lane): l
+// gets the all-pole part (lambda, from state (L1, L2)), u the whole section
+// with coefficients (b0, b1, b2) (dL/du, from state (U1, U2)).  Both share
+// the poles, hence Phi^(2^j) and Phi^lane.  Same arithmetic as two
+// pipe_section calls.
+template <int N>
+__device__ __forceinline__ void pipe_section_dual(float (&l)[N], float (&u)[N], const float a1,
+                                                  const float a2, const float b0, const float b1,
+                                                  const float b2, const float4* phi,
+                                                  const float4 lp, float& L1, float& L2,
+                                                  float& U1, float& U2) {
+    const int lane = threadIdx.x & 31;
+    // S3 for u (l has no FIR)
+    const float xl1 = u[N - 1], xl2 = u[N - 2];
+#pragma unroll
+    for (int m = N - 1; m >= 2; --m) u[m] = fmaf(b2, u[m - 2], fmaf(b1, u[m - 1], b0 * u[m]));
+    u[1] = fmaf(b1, u[0], b0 * u[1]);
+    u[0] = b0 * u[0];
+
+    // S4 (i): both particular solutions, interleaved
+    float lw0 = l[0], lw1 = fmaf(-a1, lw0, l[1]);
+    float uw0 = u[0], uw1 = fmaf(-a1, uw0, u[1]);
+#pragma unroll
+    for (int m = 2; m < N; ++m) {
+        const float lw2 = fmaf(-a1, lw1, fmaf(-a2, lw0, l[m]));
+        const float uw2 = fmaf(-a1, uw1, fmaf(-a2, uw0, u[m]));
+        lw0 = lw1;
+        lw1 = lw2;
+        uw0 = uw1;
+        uw1 = uw2;
+    }
+    float LS1 = fmaf(-a1, lw1, -a2 * lw0);
+    float LS2 = -a2 * lw1;
+    float US1 = fmaf(b1, xl1, fmaf(b2, xl2, fmaf(-a1, uw1, -a2 * uw0)));
+    float US2 = fmaf(b2, xl1, -a2 * uw1);
+
+    // S4 (ii): both lane scans
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int d = 1 << j;
+        float t1 = __shfl_up_sync(0xffffffffu, LS1, d);
+        float t2 = __shfl_up_sync(0xffffffffu, LS2, d);
+        float t3 = __shfl_up_sync(0xffffffffu, US1, d);
+        float t4 = __shfl_up_sync(0xffffffffu, US2, d);
+        t1 = lane >= d ? t1 : 0.f;
+        t2 = lane >= d ? t2 : 0.f;
+        t3 = lane >= d ? t3 : 0.f;
+        t4 = lane >= d ? t4 : 0.f;
+        const float4 ph = phi[j];
+        LS1 = fmaf(ph.x, t1, fmaf(ph.y, t2, LS1));
+        LS2 = fmaf(ph.z, t1, fmaf(ph.w, t2, LS2));
+        US1 = fmaf(ph.x, t3, fmaf(ph.y, t4, US1));
+        US2 = fmaf(ph.z, t3, fmaf(ph.w, t4, US2));
+    }
+    float LE1 = __shfl_up_sync(0xffffffffu, LS1, 1);
+    float LE2 = __shfl_up_sync(0xffffffffu, LS2, 1);
+    float UE1 = __shfl_up_sync(0xffffffffu, US1, 1);
+    float UE2 = __shfl_up_sync(0xffffffffu, US2, 1);
+    if (lane == 0) {
+        LE1 = 0.f;
+        LE2 = 0.f;
+        UE1 = 0.f;
+        UE2 = 0.f;
+    }
+    const float lz1 = fmaf(lp.x, L1, fmaf(lp.y, L2, LE1));
+    const float lz2 = fmaf(lp.z, L1, fmaf(lp.w, L2, LE2));
+    const float uz1 = fmaf(lp.x, U1, fmaf(lp.y, U2, UE1));
+    const float uz2 = fmaf(lp.z, U1, fmaf(lp.w, U2, UE2));
+
+    // S4 (iii): both re-runs, interleaved
+    l[0] = l[0] + lz1;
+    l[1] = fmaf(-a1, l[0], l[1] + lz2);
+    u[0] = u[0] + uz1;
+    u[1] = fmaf(-a1, u[0], u[1] + uz2);
+#pragma unroll
+    for (int m = 2; m < N; ++m) {
+        l[m] = fmaf(-a1, l[m - 1], fmaf(-a2, l[m - 2], l[m]));
+        u[m] = fmaf(-a1, u[m - 1], fmaf(-a2, u[m - 2], u[m]));
+    }
+
+    // the group's outgoing states, from lane 31
+    const float lo1 = fmaf(-a1, l[N - 1], -a2 * l[N - 2]);
+    const float lo2 = -a2 * l[N - 1];
+    const float uo1 = fmaf(b1, xl1, fmaf(b2, xl2, fmaf(-a1, u[N - 1], -a2 * u[N - 2])));
+    const float uo2 = fmaf(b2, xl1, -a2 * u[N - 1]);
+    L1 = __shfl_sync(0xffffffffu, lo1, 31);
+    L2 = __shfl_sync(0xffffffffu, lo2, 31);
+    U1 = __shfl_sync(0xffffffffu, uo1, 31);
+    U2 = __shfl_sync(0xffffffffu, uo2, 31);
 }
 
 // The group holding the channel's last sample, out of line: the lane chunk
