@@ -9,8 +9,9 @@ no carried channel here, and the kernel for channels within their memory
 horizon -- warp segments by default, or the section pipeline -- launched early
 behind it).  The tuning (N, W, solver, kernel) is chosen by the library's
 autotuner before the timed region.
-Prints one JSON line (rank 0), with the batched (4096 channels) and
-differentiation (forward + backward, 256 x 2^16) workloads as extra fields.
+Prints one JSON line (rank 0), with the batched (4096 channels),
+differentiation (forward + backward, 256 x 2^16) and precision-stress
+(64 x 2^26, poles at radius 0.999..0.9999) workloads as extra fields.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -149,11 +150,22 @@ def barrier(world: int):
         dist.barrier()
 
 
-def oracle_baseline(wl, target_seconds: float = 10.0):
+def oracle_baseline(wl, target_seconds: float = 10.0, checks=()):
     """Times the FP64 oracle (as it stands) on the host cores: whole-signal
-    passes of the workload, repeated until ~target_seconds of CPU work."""
+    passes of the workload, repeated until ~target_seconds of CPU work.  Also
+    runs it on each check (name, x prefix, sos rows, zi rows or None, GPU
+    output prefix, tolerance): the relative L2 error of the GPU path against the oracle on
+    causal prefixes of the benchmarked workloads."""
     import numpy as np
     import oracle
+    parity = {}
+    for name, xs, sos_c, zi_c, yg, tol in checks:
+        zi_o = None if zi_c is None else zi_c.double().numpy().reshape(1, -1, 2)
+        ref, _ = oracle.sosfilt(xs.double().numpy(), sos_c.numpy(), zi=zi_o)
+        err = float(np.linalg.norm(yg.double().numpy() - ref) / np.linalg.norm(ref))
+        prev = parity.get(name)
+        if prev is None or err > prev["rel_l2"]:
+            parity[name] = {"rel_l2": err, "tolerance": tol, "samples": int(xs.numel())}
     x = wl.x.detach().cpu().double().numpy()
     sos = wl.sos.cpu().numpy()
     K = wl.K.cpu().numpy()
@@ -172,7 +184,7 @@ def oracle_baseline(wl, target_seconds: float = 10.0):
             "kind": "oracle",
             "sample": f"{reps} full passes of the {x.size}-sample workload ({el:.1f} s); "
                       f"FP64 sample-by-sample cascade, one thread per channel",
-            "seconds": el}
+            "seconds": el, "parity": parity}
 
 
 def run_reference(args):
@@ -308,11 +320,59 @@ def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
     t_alu = fma / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
     roof = total / max(t_hbm, t_alu) / 1e9
     value = total * world / (ms * 1e-3) / 1e9
+    off = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(wl.lengths, 0)])
+    checks = []
+    for c in (0, wl.n_channels // 2, wl.n_channels - 1):
+        a = int(off[c])
+        n = min(int(wl.lengths[c]), 1 << 18)
+        k = int(wl.K[c])
+        checks.append(("batched", wl.x[a:a + n].cpu(), wl.sos[c, :k].cpu(),
+                       wl.zi[c, :k].cpu(), y[a:a + n].cpu(), 1e-5))
     return {"workload": wl.name, "channels": wl.n_channels, "samples": total,
             "value": value, "unit": "Gsamples/s", "ms_per_step": ms,
             "roofline_gsamples_per_s": roof, "frac_of_roofline": value / world / roof,
             "bound": "hbm" if t_hbm >= t_alu else "alu", "tuning": list(tuning),
-            "step": "sos_filter (prepare + apply)"}
+            "step": "sos_filter (prepare + apply)"}, checks
+
+
+def stress_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 3):
+    """Precision stress: 64 x 2^26 samples, K = 8, poles at radius
+    0.999..0.9999 (every channel carried by the look-back), one prepare +
+    apply per step.  Returns the leg's figures and the first 2^20 outputs of
+    the first and last channels (causal prefixes) for the oracle check."""
+    import torch
+    from synth import workloads
+    wl = workloads.precision_stress(device=dev)
+    plan = P.SosFilter(wl.lengths, wl.kmax, device=dev)
+    y = torch.empty_like(wl.x)
+    zf = torch.empty(wl.n_channels, wl.kmax, 2, device=dev)
+    plan(wl.x, wl.sos, wl.K, None, y=y, zf=zf)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        plan(wl.x, wl.sos, wl.K, None, y=y, zf=zf)
+    e1.record()
+    torch.cuda.synchronize()
+    if plan.device_status() != 0:
+        raise RuntimeError("stress leg: device status")
+    ms = reduce_max(e0.elapsed_time(e1) / steps, world)
+    hz, _ = plan.plan_info()
+    n = 1 << 20
+    L = int(wl.lengths[0])
+    checks = [("stress", wl.x[c * L:c * L + n].cpu(), wl.sos[c].cpu(), None,
+               y[c * L:c * L + n].cpu(), 1e-3) for c in (0, wl.n_channels - 1)]
+    total = wl.total
+    fma = 49.0 * total
+    t_hbm = 8.0 * total / (hbm_gbs * 1e9)
+    t_alu = fma / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
+    roof = total / max(t_hbm, t_alu) / 1e9
+    value = total * world / (ms * 1e-3) / 1e9
+    return {"workload": wl.name, "channels": wl.n_channels, "samples": total,
+            "value": value, "unit": "Gsamples/s", "ms_per_step": ms,
+            "roofline_gsamples_per_s": roof, "frac_of_roofline": value / world / roof,
+            "carried_channels": int((hz < 0).sum()),
+            "tuning": list(plan.tuning), "step": "sos_filter (prepare + apply)"}, checks
 
 
 def backward_leg(P, dev, world, steps: int = 5):
@@ -475,20 +535,8 @@ def main():
     if not args.no_e2e:
         e2e_value, e2e_ms = end_to_end(P, x, sos, stream, samples, world, args, plan.tuning)
 
-    # quick parity sanity
-    # quick parity sanity on a prefix (causal: the first n outputs of the full
-    # run equal the oracle on the first n inputs)
-    parity = None
-    if rank == 0:
-        try:
-            import numpy as np
-            import oracle
-            n = 1 << 20
-            yref, _ = oracle.sosfilt(x[:n].double().cpu().numpy(), sos.cpu().numpy())
-            yg = y[:n].double().cpu().numpy()
-            parity = float(np.linalg.norm(yg - yref) / np.linalg.norm(yref))
-        except Exception as exc:  # noqa: BLE001
-            parity = f"unavailable: {exc}"
+    # causal prefix of the output for the oracle check of the cpu_baseline leg
+    checks = [("bandpass16", x[:1 << 20].cpu(), sos[0].cpu(), None, y[:1 << 20].cpu(), 1e-5)]
 
     peaks, src = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -501,12 +549,16 @@ def main():
     hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     roof_samples = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / fmas) / 1e9
 
-    batched = None if args.no_extra else batched_leg(P, dev, world, sms, sm_max, hbm_gbs)
-    backward = None if args.no_extra else backward_leg(P, dev, world)
+    batched = backward = stress = None
+    if not args.no_extra:
+        batched, c_b = batched_leg(P, dev, world, sms, sm_max, hbm_gbs)
+        backward = backward_leg(P, dev, world)
+        stress, c_s = stress_leg(P, dev, world, sms, sm_max, hbm_gbs)
+        checks += c_b + c_s
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(workloads.plain_bandpass16(n=1 << 24, device="cpu"))
+        cpu = oracle_baseline(workloads.plain_bandpass16(n=1 << 24, device="cpu"), checks=checks)
 
     line = {
         "metric": "Gsamples/s K=8 FP32 (batched/plain) and % roofline at rel-L2<=1e-5 vs FP64",
@@ -544,8 +596,9 @@ def main():
         "gpu_launches": 3 * args.steps,
         "batched": batched,
         "backward": backward,
+        "stress": stress,
         "clocks": clocks,
-        "parity_rel_l2_prefix": parity,
+        "parity": cpu["parity"] if cpu else None,
         "cpu_baseline": cpu,
     }
     if rank == 0:

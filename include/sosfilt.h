@@ -100,12 +100,14 @@ typedef enum sos_status {
  * Cross-tile state.  The plan bounds each channel's impulse-response tail by
  * partial fractions over its poles and finds its memory horizon P: the warm-up
  * after which the state a tile would drop changes the output by less than
- * 2^-30 relative.  If P <= S/2 (S the segment length, a multiple of 32 N
- * chosen from the call's total length), the channel is cut into segments that
- * each start P samples early from zero state (no cross-segment dependency);
- * otherwise (poles near or on the unit circle, coincident poles) the DF2T
- * state of every section is carried by a decoupled look-back composing
- * FP64-accurate affine maps (Sec. V's group hand-off made parallel). */
+ * 2^-30 relative.  The channel is then cut into segments of S samples (the
+ * call's segment length, a multiple of 32 N chosen from its total length, or
+ * 2 P rounded up to whole groups when that is longer) that each start P
+ * samples early from zero state (no cross-segment dependency).  Where no
+ * horizon can be bounded (a pole within 1e-7 of the unit circle, coincident
+ * poles), the DF2T state of every section is carried by a decoupled
+ * look-back composing FP64-accurate affine maps (Sec. V's group hand-off made
+ * parallel). */
 typedef struct sos_tuning {
     int32_t n_blocks;
     int32_t warps;

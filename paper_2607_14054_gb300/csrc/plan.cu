@@ -70,12 +70,25 @@ __device__ __forceinline__ float cabs_(cpx a) { return hypotf(a.re, a.im); }
 // exactly such a tail of the input's convolution; P is the smallest multiple
 // of 16 (and >= 2K) for which each pole's share is below kHorizonEps *
 // ||h||_2 / (2K), with ||h||_2 bounded from below by half the norm of the
-// first 32 samples (horizon_norm, filtered in FP32).  The initial state's
+// first 32 samples (horizon_norm, filtered in FP32) or, where it is larger
+// and its sum does not cancel, by half the closed-form norm of the response
+// past sample 0 from the residues (horizon_poles).  The initial state's
 // response (DF2T state (k, j) responds with z^-j / A_k(z) * prod_{m > k}
 // B_m / A_m) must likewise have decayed below the bound at the end of the
 // first segment.  The horizon is -1 when no such P <= T / 2 exists, when a
 // pole lies on or outside |z| = 1 - 1e-7, or when two poles are closer than
 // 1e-4 (relative), where the partial fractions are not reliable.
+
+// The horizon is scale-free in the numerators: every section's (b0, b1, b2)
+// enters divided by m_k = max |b_j| (cascades of unit-peak sections near the
+// unit circle have gains far below FP32's range), the input response then
+// scaling by 1 / prod m_k.  The initial state's response, which does not
+// pass through the sections before its own, is compared in the log domain
+// with those factors put back.
+__device__ __forceinline__ float num_scale(const float* row) {
+    const float m = fmaxf(fabsf(row[0]), fmaxf(fabsf(row[1]), fabsf(row[2])));
+    return m > 0.f ? m : 1.f;
+}
 
 // ||h||_2 lower bound: half the norm of the first 32 samples of the impulse
 // response, by a systolic pipeline over the lanes (lane k < K runs section k
@@ -84,8 +97,9 @@ __device__ __forceinline__ float cabs_(cpx a) { return hypotf(a.re, a.im); }
 __device__ float horizon_norm(const float (*rowsf)[5], int K, int lane) {
     float e2 = 0.f;
     const bool on = lane < K;
-    const float cb0 = on ? rowsf[lane][0] : 1.f, cb1 = on ? rowsf[lane][1] : 0.f,
-                cb2 = on ? rowsf[lane][2] : 0.f, ca1 = on ? rowsf[lane][3] : 0.f,
+    const float im = on ? 1.f / num_scale(rowsf[lane]) : 1.f;
+    const float cb0 = on ? rowsf[lane][0] * im : 1.f, cb1 = on ? rowsf[lane][1] * im : 0.f,
+                cb2 = on ? rowsf[lane][2] * im : 0.f, ca1 = on ? rowsf[lane][3] : 0.f,
                 ca2 = on ? rowsf[lane][4] : 0.f;
     float z1 = 0.f, z2 = 0.f, y = 0.f;
     for (int t = 0; t < 32 + K - 1; ++t) {
@@ -103,13 +117,16 @@ __device__ float horizon_norm(const float (*rowsf)[5], int K, int lane) {
     return 0.5f * sqrtf(e2);
 }
 
-// Per-pole terms of the bound that do not depend on ||h||_2 (one warp, lane
-// i < 2K takes pole i): la = log(kHorizonEps (1 - r) / (2K |R_i|)) and
-// ilr = 1 / log r, so that pole i needs P >= (la + log ||h||_2) ilr, and zs =
-// the initial-state response's bound at the end of the first segment.
-// Returns false (for every lane) where the partial fractions are unusable.
-__device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], int K, int64_t T,
-                              int lane, cpx* s_pole, float& la, float& ilr, float& zs) {
+// Per-pole terms of the bound that do not depend on ||h||_2 or on the
+// segment length (one warp, lane i < 2K takes pole i): la = log(kHorizonEps
+// (1 - r) / (2K |R_i|)) and ilr = 1 / log r, so that pole i needs P >= (la +
+// log ||h||_2) ilr; zs = the log of the initial-state response's bound
+// (relative to the normalised input response), which decays as r^T over a
+// first segment of T samples (lr = log r).  Returns false (for every lane)
+// where the partial fractions are unusable.
+__device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], int K, int lane,
+                              cpx* s_pole, cpx* s_res, float& la, float& ilr, float& zs, float& lr,
+                              float& etail) {
     const int np = 2 * K;
     // poles: lane i < 2K takes root (i & 1) of z^2 + a1 z + a2 of section i / 2
     if (lane < np) {
@@ -130,6 +147,8 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
     la = 0.f;
     ilr = 0.f;
     zs = 0.f;
+    lr = 0.f;
+    cpx res{0.f, 0.f};
     if (lane < np) {
         const cpx pi = s_pole[lane];
         const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
@@ -143,7 +162,16 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
             // the poles of sections >= k (except p_i) of (1 - p_l / p_i),
             // num = prod_{m > k} B_m(p_i), B_m(z) = b0 + b1 z^-1 + b2 z^-2
             cpx num{1.f, 0.f}, den{1.f, 0.f};
-            float rz2 = 0.f;
+            // log of the largest state response (unit state, true scale)
+            // relative to the normalised input response
+            float lz2 = -INFINITY;
+            float lcum[kMaxSections];  // sum_{m <= k} log m_m
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < kMaxSections; ++k) {
+                if (k < K) acc += logf(num_scale(rowsf[k]));
+                lcum[k] = acc;
+            }
             const int own = lane >> 1;
             for (int k = K - 1; k >= 0; --k) {
 #pragma unroll
@@ -158,42 +186,84 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
                 }
                 if (k <= own) {
                     // states (k, 0) and (k, 1): |residue|^2 = |num|^2 / |den|^2
-                    // (times |1 / p_i|^2 for j = 1)
-                    const float a = fmaf(num.re, num.re, num.im * num.im) /
-                                    fmaf(den.re, den.re, den.im * den.im);
-                    rz2 = fmaxf(rz2, a * fmaxf(1.f, ir2));
+                    // (times |1 / p_i|^2 for j = 1), back to true scale
+                    float lk = 0.f;
+#pragma unroll
+                    for (int q = 0; q < kMaxSections; ++q)
+                        if (q == k) lk = lcum[q];
+                    const float a = logf(fmaf(num.re, num.re, num.im * num.im)) -
+                                    logf(fmaf(den.re, den.re, den.im * den.im)) +
+                                    logf(fmaxf(1.f, ir2)) - 2.f * lk;
+                    lz2 = fmaxf(lz2, a);
                 }
-                const float b0 = rowsf[k][0], b1 = rowsf[k][1], b2 = rowsf[k][2];
+                const float ims = 1.f / num_scale(rowsf[k]);
+                const float b0 = rowsf[k][0] * ims, b1 = rowsf[k][1] * ims, b2 = rowsf[k][2] * ims;
                 const cpx Bk{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
                 num = cmul(num, Bk);
             }
-            // full cascade: num = prod_m B_m(p_i), den over all other poles
+            // full cascade: num = prod_m B_m(p_i), den over all other poles;
+            // the residue R_i = num / den of h[n] = sum_i R_i p_i^n (n >= 1)
+            res = cdiv(num, den);
             const float R = sqrtf(fmaf(num.re, num.re, num.im * num.im) /
                                   fmaf(den.re, den.re, den.im * den.im));
+            lr = logf(r);
             if (R > 0.f) {
                 la = logf(kHorizonEps * (1.f - r) / ((float)np * R));
-                ilr = 1.f / logf(r);
+                ilr = 1.f / lr;
             }
-            zs = sqrtf(rz2) * powf(r, (float)T) / (1.f - r);
+            // log of the initial-state response bound, before its r^T decay
+            zs = 0.5f * lz2 - logf(1.f - r);
             if (!(fabsf(la) < 1e30f) || !(zs < 1e30f)) bad = true;
         }
     }
+    // the energy of the response past sample 0, sum_{n>=1} |h[n]|^2 =
+    // Re sum_{i,j} R_i conj(R_j) q / (1 - q), q = p_i conj(p_j), with the sum
+    // of the terms' magnitudes beside it (how much the sum cancels)
+    if (lane < np) s_res[lane] = res;
+    __syncwarp();
+    float e = 0.f, eabs = 0.f;
+    if (lane < np) {
+        const cpx pi = s_pole[lane];
+        for (int j = 0; j < np; ++j) {
+            const cpx pj = s_pole[j], rj = s_res[j];
+            const cpx q = cmul(pi, cpx{pj.re, -pj.im});
+            const cpx t = cdiv(cmul(cmul(res, cpx{rj.re, -rj.im}), q), cpx{1.f - q.re, -q.im});
+            e += t.re;
+            eabs += cabs_(t);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        e += __shfl_xor_sync(0xffffffffu, e, o);
+        eabs += __shfl_xor_sync(0xffffffffu, eabs, o);
+    }
+    etail = (e > 0.f && e >= 1e-4f * eabs && e < 1e30f) ? e : 0.f;
     return !__any_sync(0xffffffffu, bad);
 }
 
-// The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp).
-__device__ int horizon_combine(bool ok, float h2, int K, int64_t T, float la, float ilr,
-                               float zs) {
+// The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp), and
+// the channel's segment length: the call's T, or longer when the horizon
+// needs it (a segment is at least 2 P and long enough for the initial
+// state's response to decay below the bound, rounded up to whole groups of
+// G), so that long-memory channels keep a bounded warm-up instead of being
+// carried.  -1 where no horizon holds.
+__device__ int horizon_combine(bool ok, float h2, int K, int64_t T, int64_t G, float la, float ilr,
+                               float zs, float lr, int64_t& seg) {
     float ptail = ilr != 0.f ? (la + logf(h2)) * ilr : 0.f;
-    float zsum = zs;
+    // the initial state's response (each pole's share counted 2K times) has
+    // decayed below the bound after tz samples
+    const float lb = logf(kHorizonEps * h2 / (float)(2 * K));
+    float tz = (lr < 0.f && zs > -1e30f) ? (lb - zs) / lr : 0.f;
     for (int o = 16; o > 0; o >>= 1) {
         ptail = fmaxf(ptail, __shfl_xor_sync(0xffffffffu, ptail, o));
-        zsum += __shfl_xor_sync(0xffffffffu, zsum, o);
+        tz = fmaxf(tz, __shfl_xor_sync(0xffffffffu, tz, o));
     }
-    if (!ok || !(h2 > 0.f) || !(ptail < 1e9f) || !(zsum <= kHorizonEps * h2)) return -1;
+    if (!ok || !(h2 > 0.f) || !(ptail < 1e9f) || !(tz < 1e9f)) return -1;
     const float need = fmaxf(ptail, (float)(2 * K));
     const int64_t P = ((int64_t)ceilf(need) + 15) / 16 * 16;
-    return P <= T / 2 ? (int)P : -1;
+    int64_t want = 2 * P > (int64_t)ceilf(tz) ? 2 * P : (int64_t)ceilf(tz);
+    seg = T;
+    if (want > seg) seg = (want + G - 1) / G * G;
+    return (int)P;
 }
 
 // Block C: the channel table.
@@ -287,6 +357,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     __shared__ float s_h2;                      // ||h||_2 lower bound
     __shared__ int s_mode, s_horizon, s_err;
     __shared__ cpx s_pole[2 * kMaxSections];
+    __shared__ cpx s_res[2 * kMaxSections];
     // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
     __shared__ dfm2 s_chain[kMaxSections][20];
 
@@ -378,11 +449,17 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
         // the segment length) and its work units: segments when it has a
         // horizon, look-back tiles otherwise
         const int64_t T = (int64_t)p.W * kLanes * p.N;
-        float la = 0.f, ilr = 0.f, zs = 0.f;
-        const bool ok = !carry_only &&
-                        horizon_poles(s_row, s_rowf, Kc, p.seg, lane, s_pole, la, ilr, zs);
+        float la = 0.f, ilr = 0.f, zs = 0.f, lr = 0.f, etail = 0.f;
+        const bool ok = !carry_only && horizon_poles(s_row, s_rowf, Kc, lane, s_pole, s_res, la,
+                                                     ilr, zs, lr, etail);
         asm volatile("bar.sync 3, 64;" ::: "memory");
-        int P = carry_only ? -1 : horizon_combine(ok, s_h2, Kc, p.seg, la, ilr, zs);
+        // ||h||_2 from below: the first 32 samples, or half the closed-form
+        // norm of the response past sample 0 where that sum is well
+        // conditioned (slow-building responses of poles near the unit circle)
+        const float h2 = fmaxf(s_h2, 0.5f * sqrtf(etail));
+        int64_t seg = p.seg;
+        int P = carry_only ? -1
+                           : horizon_combine(ok, h2, Kc, p.seg, 32LL * p.N, la, ilr, zs, lr, seg);
         // backward plans have no look-back: a channel without a horizon is
         // one segment, run from its start to its end by one pipeline
         const int single = (P < 0 && (p.flags_opt & kFlagBackwardPlan)) ? 1 : 0;
@@ -393,10 +470,11 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             int64_t nt;
             if (len == 0) nt = 0;
             else if (single) nt = 1;
-            else if (P >= 0) nt = (len + p.seg - 1) / p.seg;
+            else if (P >= 0) nt = (len + seg - 1) / seg;
             else nt = (len + T - 1) / T;
             p.chan[c].horizon = P;
             p.chan[c].single = single;
+            p.chan[c].seg = P >= 0 ? seg : p.seg;
             p.chan[c].ntiles = (int32_t)nt;
             s_horizon = P;
         }
@@ -446,7 +524,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
         dfm2 C{df_neg(e), df_neg(f), df{1.f, 0.f}, df{0.f, 0.f}};
         for (int j = 0; j < 5; ++j) {
             o->cr_tpow[j] = to_f4(C);
-            C = dfm_mul_fast(C, C);
+            C = dfm_mul(C, C);
         }
         const bool ok = kappa <= kCrKappaMax;
         o->cr_misc = make_float4(df_to_float(e), df_to_float(f), kappa, ok ? 1.f : 0.f);
@@ -460,10 +538,11 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
     CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
     {
-        // Phi^lane by binary powering (the cheaper products: rounded to FP32)
+        // Phi^lane by binary powering (exact additions: for poles near the
+        // unit circle the entries come out of near-cancelling sums)
         dfm2 P = dfm_identity();
         for (int j = 0; j < 5; ++j)
-            if ((lane >> j) & 1) P = dfm_mul_fast(P, s_chain[k][j]);
+            if ((lane >> j) & 1) P = dfm_mul(P, s_chain[k][j]);
         out32->lane_pow[lane] = to_f4(P);
     }
     if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);

@@ -54,11 +54,13 @@ struct ChanInfo {
     int32_t ntiles;   // tiles of this channel (dispatch)
     int32_t err;      // coefficient error found by the plan kernel (sos_status), 0 if none
     int64_t slot;     // first look-back slot of the channel (ceil(len / T) slots)
-    int32_t horizon;  // >= 0: memory horizon P (tiles overlap by P samples, no carry);
-                      // -1: the state is carried by the look-back
-    int32_t single;   // 1: the whole channel is one pipeline segment (backward plans)
+    int32_t horizon;  // >= 0: memory horizon P (segments start P samples early, no
+                      // carry); -1: the state is carried by the look-back
+    int32_t single;   // 1: the whole channel is one segment (backward plans)
+    int64_t seg;      // segment length of a channel with a horizon (a multiple of 32 N,
+                      // at least 2 P)
 };
-static_assert(sizeof(ChanInfo) == 48, "channel table entry");
+static_assert(sizeof(ChanInfo) == 56, "channel table entry");
 
 // A channel's memory horizon P is the shortest warm-up after which the
 // cascade's impulse-response tail, summed in absolute value, is below

@@ -41,8 +41,8 @@ __device__ __forceinline__ SegGeom seg_geom(const Params& p, int64_t d) {
     g.len = ci.len;
     g.K = ci.K;
     g.horizon = ci.horizon;
-    g.out_lo = (int64_t)g.si * p.seg;
-    g.out_hi = (ci.single || g.out_lo + p.seg >= ci.len) ? ci.len : g.out_lo + p.seg;
+    g.out_lo = (int64_t)g.si * ci.seg;
+    g.out_hi = (ci.single || g.out_lo + ci.seg >= ci.len) ? ci.len : g.out_lo + ci.seg;
     g.cstart = g.si == 0 ? 0 : g.out_lo - ci.horizon;
     g.ngroups = (int)((g.out_hi - g.cstart + kGroup - 1) / kGroup);
     return g;

@@ -259,15 +259,19 @@ def test_horizons_bound_the_true_impulse_tail():
     hz, tiles = plan.plan_info()
     hz, tiles = hz.numpy(), tiles.numpy()
     T = 32 * 32 * 8
-    assert hz[65] == -1 and hz[68] == -1
+    # coincident poles: no reliable partial fractions, carried by the look-back
+    assert hz[65] == -1
+    # long memory: a horizon longer than a default segment (the channel then
+    # gets segments of at least 2 P), or carried
+    assert hz[68] == -1 or hz[68] > 4096
     for c in range(C):
         L = 50_000
         if hz[c] < 0:
             assert tiles[c] == -(-L // T)
             continue
-        # pipelined channel: segments of at most 64 groups, warm-up <= half
-        assert hz[c] % 16 == 0 and 2 * int(K[c]) <= hz[c] <= 32 * 1024
-        assert 1 <= tiles[c] <= -(-L // (8 * 1024))
+        assert hz[c] % 16 == 0 and 2 * int(K[c]) <= hz[c]
+        # segments of at least 8 groups and at least 2 P
+        assert 1 <= tiles[c] <= -(-L // max(8 * 1024, 2 * int(hz[c])))
         h = _impulse_response(sos[c, :K[c]], 1 << 17)
         tail = np.abs(h[hz[c]:]).sum()
         assert tail <= 2.0 ** -30 * np.sqrt((h ** 2).sum()), (c, hz[c], tail)
@@ -275,9 +279,9 @@ def test_horizons_bound_the_true_impulse_tail():
 
 
 def test_long_and_short_memory_channels_in_one_batch():
-    """Channels with poles at radius 0.999..0.9999 (carried by the look-back,
-    stress tolerance 1e-3) batched with short-memory channels (overlapping
-    tiles, 1e-5), interleaved dispatch."""
+    """Channels with poles at radius 0.999..0.9999 (long memory: segments of
+    at least twice their horizon, or carried by the look-back; stress
+    tolerance 1e-3) batched with short-memory channels (1e-5)."""
     P = _lib()
     from synth import filters
     lengths = [300_000, 120_000, 250_000, 90_000, 400_000, 7]
@@ -296,7 +300,9 @@ def test_long_and_short_memory_channels_in_one_batch():
     plan = P.SosFilter(torch.tensor(lengths), kmax)
     plan.prepare(args[1].cuda(), args[2].cuda())
     hz, _ = plan.plan_info()
-    assert (hz.numpy()[0:5:2] == -1).all() and (hz.numpy()[1::2] >= 0).all()
+    # long-memory channels: carried, or run in segments of at least 2 P
+    assert ((hz.numpy()[0:5:2] == -1) | (hz.numpy()[0:5:2] > 4096)).all()
+    assert (hz.numpy()[1::2] >= 0).all()
     y_ref, zf_ref = run_oracle(*args)
     err = oracle.rel_l2_per_channel(y, y_ref, np.array(lengths))
     print("long-memory rel-L2", err[0:5:2], "short", err[1::2])
