@@ -216,6 +216,10 @@ __device__ void lookback_warp(const Params& p, int64_t t, int64_t npred, int k, 
                             s2 = df_add_fast(s2, shfl_xor_df(s2, m));
                         }
                     }
+                    // with rounds skipped only lane 0 is sure to hold the
+                    // whole sum: every lane takes its value
+                    s1 = shfl_df0(s1);
+                    s2 = shfl_df0(s2);
                 }
                 if (first_window) {
                     acc1 = s1;

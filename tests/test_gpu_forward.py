@@ -336,3 +336,30 @@ def test_cyclic_reduction_ill_conditioned_level_keeps_ph():
     for N in (16, 32, 64):
         y, zf = run_gpu(args, tuning=(N, 8, 2, 0))
         check(y, zf, y_ref, zf_ref, np.array(lengths), K.numpy(), 1e-5)
+
+
+def test_lookback_long_memory_every_tile():
+    """The look-back carrying a long-memory channel (poles at radius
+    0.999..0.9999, as in the precision-stress workload) across tiles whose
+    predecessors are still running: every tile against the oracle, and two
+    calls bitwise equal.  (Each data warp takes its incoming state from the
+    coordinator's lane of the same index, so the composed state must reach
+    every lane, not lane 0 only.)"""
+    P = _lib()
+    wl = workloads.precision_stress(n_channels=2, length=1 << 16, device="cuda")
+    L = 1 << 16
+    for tuning in [(32, 8, 1, 2), (16, 8, 1, 2), (32, 4, 1, 2)]:
+        plan = P.SosFilter(wl.lengths, 8, tuning=tuning)
+        y1, _ = plan(wl.x, wl.sos, wl.K, None)
+        y2, _ = plan(wl.x, wl.sos, wl.K, None)
+        assert plan.device_status() == 0
+        assert torch.equal(y1, y2)
+        T = tuning[0] * 32 * tuning[1]
+        for c in range(2):
+            ref, _ = oracle.sosfilt(wl.x[c * L:(c + 1) * L].double().cpu().numpy(),
+                                    wl.sos[c].cpu().numpy())
+            got = y1[c * L:(c + 1) * L].double().cpu().numpy()
+            for t in range(L // T):
+                a, b = t * T, (t + 1) * T
+                err = np.linalg.norm(got[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
+                assert err <= 1e-3, (tuning, c, t, err)
