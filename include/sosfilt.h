@@ -263,6 +263,21 @@ sos_status sos_filter_backward(const float *x, const double *sos, const int32_t 
 sos_status sos_plan_query(void *workspace, int32_t first, int32_t count, int32_t *horizon,
                           int32_t *tiles, void *stream);
 
+/* Waits for `stream`, then writes for channels [first, first + count) of the
+ * most recent sos_prepare on this workspace whether some section of the
+ * channel is ill-conditioned for FP32 (1) or not (0), into extended[i] (a
+ * host array of `count` entries).  A section is, when the largest entry of
+ * its transition powers A^(N 2^j), A^(N l) exceeds 8 (a pole pair close to
+ * z = 1 or z = -1 near the unit circle): the default warp-segment kernel
+ * then runs that section's lane scan and fold (S4) in double-float and adds
+ * the low parts of a1, a2 in its in-lane recursions; the section pipeline
+ * (SOS_FLAG_SECTION_PIPELINE), the cyclic-reduction solver and the look-back
+ * kernel run every section in FP32.  No allocation.  SOS_ERR_ARG if the range
+ * is outside the channels of that call or `extended` is NULL.  This query
+ * has no counterpart in the paper. */
+sos_status sos_plan_extended(void *workspace, int32_t first, int32_t count, int32_t *extended,
+                             void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *sos_status_str(sos_status status);
 

@@ -179,6 +179,18 @@ class SosFilter:
             raise SosError(st, "sos_plan_query")
         return h, t
 
+    def plan_extended(self):
+        """Per channel, 1 where some section is ill-conditioned for FP32 and
+        the default kernel runs its lane scan in extended precision (int32
+        host tensor, from the latest prepare)."""
+        e = torch.empty(self.n_channels, dtype=torch.int32)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = _abi.sos_plan_extended(self.workspace.data_ptr(), 0, self.n_channels, e.data_ptr(),
+                                    stream)
+        if st != 0:
+            raise SosError(st, "sos_plan_extended")
+        return e
+
     def apply_part(self, part: str, x: torch.Tensor, y: torch.Tensor,
                    zi: Optional[torch.Tensor] = None, zf: Optional[torch.Tensor] = None):
         """One of the two launches of apply(): "pipeline" or "carried"."""

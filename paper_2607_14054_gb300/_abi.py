@@ -95,6 +95,8 @@ def load(build_if_missing: bool = False):
         lib.sos_filter_backward.restype = ctypes.c_int
         lib.sos_plan_query.argtypes = [vp, i32, i32, vp, vp, vp]
         lib.sos_plan_query.restype = ctypes.c_int
+        lib.sos_plan_extended.argtypes = [vp, i32, i32, vp, vp]
+        lib.sos_plan_extended.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -188,6 +190,13 @@ def sos_plan_query(ws_ptr: int, first: int, count: int, horizon_ptr: int, tiles_
     V = ctypes.c_void_p
     return int(load().sos_plan_query(V(ws_ptr), first, count, V(horizon_ptr or None),
                                      V(tiles_ptr or None), V(stream)))
+
+
+def sos_plan_extended(ws_ptr: int, first: int, count: int, extended_ptr: int,
+                      stream: int) -> int:
+    """Host pointer as an integer."""
+    V = ctypes.c_void_p
+    return int(load().sos_plan_extended(V(ws_ptr), first, count, V(extended_ptr), V(stream)))
 
 
 def sos_status_str(status: int) -> str:

@@ -10,7 +10,10 @@ precision class), and optionally in a JSON file (``SOSFILT_TUNE_CACHE``).
 
 The precision class is whether the plan carries any channel's state by the
 look-back (poles near the unit circle): only then does W, the look-back
-kernel's tile width, matter, so only then are several W tried.
+kernel's tile width, matter, so only then are several W tried.  And whether
+some section is ill-conditioned for FP32 (``SosFilter.plan_extended``): only
+the PH warp-segment kernel gives those sections extended precision, so then
+neither the section pipeline nor cyclic reduction is a candidate.
 """
 from __future__ import annotations
 
@@ -32,14 +35,15 @@ _cache: Dict[Tuple, Tuple[int, int, int, int]] = {}
 _lock = threading.Lock()
 
 
-def shape_key(lengths: Sequence[int], kmax: int, carried: bool) -> Tuple:
+def shape_key(lengths: Sequence[int], kmax: int, carried: bool, extended: bool = False) -> Tuple:
     """(max K, length bucket, channel-count bucket, precision class)."""
     n = len(lengths)
     total = sum(int(v) for v in lengths)
     mean = total / max(n, 1)
     lb = int(round(math.log2(mean))) if mean >= 1 else 0
     cb = int(round(math.log2(n))) if n >= 1 else 0
-    return (int(kmax), lb, cb, "carried" if carried else "horizon")
+    cls = "carried" if carried else "horizon"
+    return (int(kmax), lb, cb, cls + "+ext" if extended else cls)
 
 
 SECTION_PIPELINE = 4  # SOS_FLAG_SECTION_PIPELINE
@@ -58,17 +62,20 @@ KERNELS = {16: (0, ws_ctas(3), SECTION_PIPELINE),
            64: (0, ws_ctas(2), SECTION_PIPELINE)}
 
 
-def candidates(carried: bool) -> List[Tuple[int, int, int, int]]:
+def candidates(carried: bool, extended: bool = False) -> List[Tuple[int, int, int, int]]:
     """Tunings to try: every N with both solvers and each kernel choice for
     the channels within their memory horizon; several W only when some
-    channel is carried by the look-back (W sizes the look-back tiles)."""
+    channel is carried by the look-back (W sizes the look-back tiles); PH on
+    the warp-segment kernel only when some section is ill-conditioned."""
     out = []
     for n in (16, 32, 64):
         ws = sorted({w for (nn, w) in SUPPORTED_NW if nn == n}) if carried else \
             [8 if (n, 8) in SUPPORTED_NW else min(w for (nn, w) in SUPPORTED_NW if nn == n)]
         for w in ws:
-            for a in ALGOS:
+            for a in ((1,) if extended else ALGOS):
                 for f in KERNELS[n]:
+                    if extended and f & SECTION_PIPELINE:
+                        continue
                     out.append((n, w, a, f))
     return out
 
@@ -132,7 +139,8 @@ def autotune(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = Non
     probe.prepare(sos.contiguous(), K)
     hz, _ = probe.plan_info()
     carried = bool((hz < 0).any())
-    key = shape_key(lh, kmax, carried)
+    extended = bool(probe.plan_extended().any())
+    key = shape_key(lh, kmax, carried, extended)
     path = _cache_file()
     with _lock:
         if use_cache and path and not _cache:
@@ -142,7 +150,7 @@ def autotune(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = Non
     y = torch.empty_like(x)
     zf = torch.empty((C, kmax, 2), dtype=torch.float32, device=x.device)
     best, best_t = DEFAULT, float("inf")
-    for cand in candidates(carried):
+    for cand in candidates(carried, extended):
         plan = SosFilter(lh, kmax, tuning=cand, device=x.device)
         t = _time_apply(plan, x, y, zi, zf, sos.contiguous(), K, reps)
         if report is not None:

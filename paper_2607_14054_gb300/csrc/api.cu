@@ -359,6 +359,28 @@ sos_status sos_plan_query(void* workspace, int32_t first, int32_t count, int32_t
     return SOS_OK;
 }
 
+sos_status sos_plan_extended(void* workspace, int32_t first, int32_t count, int32_t* extended,
+                             void* stream) {
+    if (!workspace || !extended || first < 0 || count < 0) return SOS_ERR_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    WsHeader h;
+    if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    if ((int64_t)first + count > h.nchan) return SOS_ERR_ARG;
+    const WsLayout L = ws_layout(h.nchan, 1, 1);
+    ChanInfo buf[128];
+    for (int32_t c0 = 0; c0 < count; c0 += 128) {
+        const int32_t n = count - c0 < 128 ? count - c0 : 128;
+        if (cudaMemcpy(buf,
+                       static_cast<char*>(workspace) + L.chan + sizeof(ChanInfo) * (first + c0),
+                       sizeof(ChanInfo) * n, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return SOS_ERR_CUDA;
+        for (int32_t i = 0; i < n; ++i) extended[c0 + i] = buf[i].ext;
+    }
+    return SOS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -22,26 +22,67 @@ __device__ __forceinline__ void pick_pair(const float (&v)[N], int mq, float& q0
     }
 }
 
+// Chunk v[] <-> the lane's row, around section_zf_row.
+template <int N>
+__device__ __forceinline__ void chunk_to_row(const float (&v)[N], float* row) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q)
+        *reinterpret_cast<float4*>(row + 4 * q) =
+            make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+template <int N>
+__device__ __forceinline__ void row_to_chunk(float (&v)[N], const float* row) {
+#pragma unroll
+    for (int q = 0; q < N / 4; ++q) {
+        const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+        v[4 * q + 0] = t.x;
+        v[4 * q + 1] = t.y;
+        v[4 * q + 2] = t.z;
+        v[4 * q + 3] = t.w;
+    }
+}
+
+
 // One section over one group, lane chunk v[] in registers, from the group's
 // incoming DF2T state (Z1, Z2) (scaled by 1/G_k when b0 is factored); leaves
 // the group's outgoing state in (Z1, Z2).  ZF: the group holds the channel's
 // last sample (at element mq of the chunk of the lane where zf_owner is set),
 // whose DF2T state goes to zf_dst; a separate instantiation, so that other
-// groups do not run the selects it needs.  s_own is unused (kept for the
-// callers' signature).
+// groups do not run the selects it needs.  s_own: the lane's row (N floats,
+// 16-byte aligned), scratch for DFS.
 // INJ: a DF2T state (zi1, zi2) enters at group-relative sample pinj instead
 // of the group start (the inputs before it being zero): added to the
 // all-pole input at pinj and pinj + 1 (the backward's recompute of a
 // channel's first group, whose grid is anchored elsewhere).
 // NOFIR: the all-pole part alone (b0 = 1, b1 = b2 = 0): S3 is skipped.
-template <int N, bool FACT, bool ZF = false, bool INJ = false, bool NOFIR = false>
+// DFS: extended precision for ill-conditioned sections: the lane scan and the
+// fold run in double-float, with the powers' low parts phi_lo and lpl beside
+// phi and lp, and the in-lane recursions add the low parts alo of a1, a2
+// (the samples stay FP32).
+template <int N, bool FACT, bool ZF = false, bool INJ = false, bool NOFIR = false,
+          bool DFS = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
                                              float* zf_dst, float G, int pinj = -1,
-                                             float zi1 = 0.f, float zi2 = 0.f) {
+                                             float zi1 = 0.f, float zi2 = 0.f,
+                                             const float4* phi_lo = nullptr,
+                                             float4 lpl = {0.f, 0.f, 0.f, 0.f},
+                                             float2 alo = {0.f, 0.f}) {
     const int lane = threadIdx.x & 31;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
+    // the all-pole terms, with a_i = ab + alo for DFS (the low-part products
+    // go first, into the smaller terms), FP32 a_i otherwise:
+    // ap2 = t - a1 y1 - a2 y2, ap1 = t - a1 y1, st2 = -a1 y1 - a2 y2, st1 = -a2 y
+    auto ap2 = [&](float y1, float y2, float t) {
+        return fmaf(-a1, y1, fmaf(-a2, y2, DFS ? fmaf(-alo.x, y1, fmaf(-alo.y, y2, t)) : t));
+    };
+    auto ap1 = [&](float y1, float t) { return fmaf(-a1, y1, DFS ? fmaf(-alo.x, y1, t) : t); };
+    auto st2 = [&](float y1, float y2) {
+        return fmaf(-a1, y1, DFS ? fmaf(-a2, y2, fmaf(-alo.x, y1, -alo.y * y2)) : -a2 * y2);
+    };
+    auto st1 = [&](float y) { return DFS ? fmaf(-a2, y, -alo.y * y) : -a2 * y; };
 
     // S8 support: the section input at the channel's last sample (element mq
     // of the owner's chunk), picked by compile-time-indexed selects
@@ -66,46 +107,79 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     }
 
     // S4 (i): particular solution from zero state, terminal values only
-    float w0 = v[0], w1 = fmaf(-a1, w0, v[1]);
+    float w0 = v[0], w1 = ap1(w0, v[1]);
 #pragma unroll
     for (int m = 2; m < N; ++m) {
-        const float w2 = fmaf(-a1, w1, fmaf(-a2, w0, v[m]));
+        const float w2 = ap2(w1, w0, v[m]);
         w0 = w1;
         w1 = w2;
     }
-    float S1 = fmaf(b1, xl1, fmaf(b2, xl2, fmaf(-a1, w1, -a2 * w0)));
-    float S2 = fmaf(b2, xl1, -a2 * w1);
+    float S1 = fmaf(b1, xl1, fmaf(b2, xl2, st2(w1, w0)));
+    float S2 = fmaf(b2, xl1, st1(w1));
 
-    // S4 (ii): inclusive scan over lanes, z_{l+1} = Phi z_l + s_l
+    float zin1, zin2;
+    if (DFS) {
+        // S4 (ii) and the fold in double-float; the chunk waits in the lane's
+        // row (s_own) meanwhile, so that its registers serve the scan
+        chunk_to_row<N>(v, s_own);
+        df s1 = df_from(S1), s2 = df_from(S2);
 #pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const int d = 1 << j;
-        float t1 = __shfl_up_sync(0xffffffffu, S1, d);
-        float t2 = __shfl_up_sync(0xffffffffu, S2, d);
-        t1 = lane >= d ? t1 : 0.f;
-        t2 = lane >= d ? t2 : 0.f;
-        S1 = fmaf(phi[j].x, t1, fmaf(phi[j].y, t2, S1));
-        S2 = fmaf(phi[j].z, t1, fmaf(phi[j].w, t2, S2));
+        for (int j = 0; j < 5; ++j) {
+            const int d = 1 << j;
+            df t1{__shfl_up_sync(0xffffffffu, s1.hi, d), __shfl_up_sync(0xffffffffu, s1.lo, d)};
+            df t2{__shfl_up_sync(0xffffffffu, s2.hi, d), __shfl_up_sync(0xffffffffu, s2.lo, d)};
+            if (lane < d) {
+                t1 = df_from(0.f);
+                t2 = df_from(0.f);
+            }
+            const float4 h = phi[j], l = phi_lo[j];
+            s1 = df_add_fast(s1, df_add_fast(df_mul(df{h.x, l.x}, t1), df_mul(df{h.y, l.y}, t2)));
+            s2 = df_add_fast(s2, df_add_fast(df_mul(df{h.z, l.z}, t1), df_mul(df{h.w, l.w}, t2)));
+        }
+        df e1{__shfl_up_sync(0xffffffffu, s1.hi, 1), __shfl_up_sync(0xffffffffu, s1.lo, 1)};
+        df e2{__shfl_up_sync(0xffffffffu, s2.hi, 1), __shfl_up_sync(0xffffffffu, s2.lo, 1)};
+        if (lane == 0) {
+            e1 = df_from(0.f);
+            e2 = df_from(0.f);
+        }
+        const df z1 = df_from(Z1), z2 = df_from(Z2);
+        zin1 = df_to_float(df_add_fast(
+            e1, df_add_fast(df_mul(df{lp.x, lpl.x}, z1), df_mul(df{lp.y, lpl.y}, z2))));
+        zin2 = df_to_float(df_add_fast(
+            e2, df_add_fast(df_mul(df{lp.z, lpl.z}, z1), df_mul(df{lp.w, lpl.w}, z2))));
+        row_to_chunk<N>(v, s_own);
+    } else {
+        // S4 (ii): inclusive scan over lanes, z_{l+1} = Phi z_l + s_l
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int d = 1 << j;
+            float t1 = __shfl_up_sync(0xffffffffu, S1, d);
+            float t2 = __shfl_up_sync(0xffffffffu, S2, d);
+            t1 = lane >= d ? t1 : 0.f;
+            t2 = lane >= d ? t2 : 0.f;
+            S1 = fmaf(phi[j].x, t1, fmaf(phi[j].y, t2, S1));
+            S2 = fmaf(phi[j].z, t1, fmaf(phi[j].w, t2, S2));
+        }
+        float E1 = __shfl_up_sync(0xffffffffu, S1, 1);
+        float E2 = __shfl_up_sync(0xffffffffu, S2, 1);
+        if (lane == 0) {
+            E1 = 0.f;
+            E2 = 0.f;
+        }
+        // fold the group's incoming state into this lane's: Phi^lane Z + E
+        zin1 = fmaf(lp.x, Z1, fmaf(lp.y, Z2, E1));
+        zin2 = fmaf(lp.z, Z1, fmaf(lp.w, Z2, E2));
     }
-    float E1 = __shfl_up_sync(0xffffffffu, S1, 1);
-    float E2 = __shfl_up_sync(0xffffffffu, S2, 1);
-    if (lane == 0) {
-        E1 = 0.f;
-        E2 = 0.f;
-    }
-    // fold the group's incoming state into this lane's: Phi^lane Z + E
-    const float zin1 = fmaf(lp.x, Z1, fmaf(lp.y, Z2, E1));
-    const float zin2 = fmaf(lp.z, Z1, fmaf(lp.w, Z2, E2));
 
     // S4 (iii): re-run the recursion from the true incoming state
     v[0] = v[0] + zin1;
-    v[1] = fmaf(-a1, v[0], v[1] + zin2);
+    v[1] = ap1(v[0], v[1] + zin2);
 #pragma unroll
-    for (int m = 2; m < N; ++m) v[m] = fmaf(-a1, v[m - 1], fmaf(-a2, v[m - 2], v[m]));
+    for (int m = 2; m < N; ++m) v[m] = ap2(v[m - 1], v[m - 2], v[m]);
 
     // the group's outgoing state, from lane 31's last two inputs and outputs
-    const float o1 = fmaf(b1, xl1, fmaf(b2, xl2, fmaf(-a1, v[N - 1], -a2 * v[N - 2])));
-    const float o2 = fmaf(b2, xl1, -a2 * v[N - 1]);
+    const float o1 = fmaf(b1, xl1, fmaf(b2, xl2, st2(v[N - 1], v[N - 2])));
+    const float o2 = fmaf(b2, xl1, st1(v[N - 1]));
     Z1 = __shfl_sync(0xffffffffu, o1, 31);
     Z2 = __shfl_sync(0xffffffffu, o2, 31);
     // a state injected at the group's last sample: its second component
@@ -117,9 +191,9 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
         float yq, yqm1;
         pick_pair<N>(v, mq, yq, yqm1);
         float f1;
-        if (mq >= 1) f1 = fmaf(b1, xq, fmaf(b2, xqm1, fmaf(-a1, yq, -a2 * yqm1)));
-        else f1 = fmaf(b1, xq, fmaf(-a1, yq, zin2));
-        const float f2 = fmaf(b2, xq, -a2 * yq);
+        if (mq >= 1) f1 = fmaf(b1, xq, fmaf(b2, xqm1, st2(yq, yqm1)));
+        else f1 = fmaf(b1, xq, ap1(yq, zin2));
+        const float f2 = fmaf(b2, xq, st1(yq));
         if (zf_owner) {
             zf_dst[0] = f1 * G;
             zf_dst[1] = f2 * G;
@@ -373,27 +447,6 @@ __device__ __noinline__ float2 section_zf_row(float* row, const float4 ab, const
             make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
     __syncwarp();
     return z;
-}
-
-// Chunk v[] <-> the lane's row, around section_zf_row.
-template <int N>
-__device__ __forceinline__ void chunk_to_row(const float (&v)[N], float* row) {
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q)
-        *reinterpret_cast<float4*>(row + 4 * q) =
-            make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-}
-
-template <int N>
-__device__ __forceinline__ void row_to_chunk(float (&v)[N], const float* row) {
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q) {
-        const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
-        v[4 * q + 0] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
 }
 
 }  // namespace sosf

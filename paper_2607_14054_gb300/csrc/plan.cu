@@ -39,6 +39,41 @@ __device__ __forceinline__ float4 to_f4(const dfm2& m) {
     return make_float4(df_to_float(m.a), df_to_float(m.b), df_to_float(m.c), df_to_float(m.d));
 }
 
+// what to_f4 dropped: x - to_f4(x) per entry, the low word of the stored
+// double-float power
+__device__ __forceinline__ float df_rest(df x) {
+    const float h = df_to_float(x);
+    return (x.hi - h) + x.lo;
+}
+
+__device__ __forceinline__ float4 to_f4_lo(const dfm2& m) {
+    return make_float4(df_rest(m.a), df_rest(m.b), df_rest(m.c), df_rest(m.d));
+}
+
+__device__ __forceinline__ float max_entry(const dfm2& m) {
+    return fmaxf(fmaxf(fabsf(m.a.hi), fabsf(m.b.hi)), fmaxf(fabsf(m.c.hi), fabsf(m.d.hi)));
+}
+
+// How far rounding a1, a2 to FP32 moves the poles of z^2 + a1 z + a2,
+// relative to their distance from the unit circle: |dp| <= (r |da1| + |da2|)
+// / |p1 - p2| (first order, from p^2 + a1 p + a2 = 0), over 1 - r.
+// Infinite for a double pole or one on or outside the circle.
+__device__ __forceinline__ double coef_sensitivity(double a1, double a2) {
+    const double da1 = a1 - (double)(float)a1, da2 = a2 - (double)(float)a2;
+    const double disc = a1 * a1 - 4.0 * a2;
+    double r, sep;
+    if (disc < 0.0) {
+        r = sqrt(a2);
+        sep = sqrt(-disc);
+    } else {
+        sep = sqrt(disc);
+        r = fmax(fabs(-a1 + sep), fabs(-a1 - sep)) * 0.5;
+    }
+    const double gap = 1.0 - r;
+    if (!(sep > 0.0) || !(gap > 0.0)) return INFINITY;
+    return (r * fabs(da1) + fabs(da2)) / (sep * gap);
+}
+
 __device__ __forceinline__ bool finite_row(const double* r) {
     for (int i = 0; i < 6; ++i)
         if (!isfinite(r[i])) return false;
@@ -169,7 +204,7 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
             float acc = 0.f;
 #pragma unroll
             for (int k = 0; k < kMaxSections; ++k) {
-                if (k < K) acc += logf(num_scale(rowsf[k]));
+                if (k < K) acc += __logf(num_scale(rowsf[k]));
                 lcum[k] = acc;
             }
             const int own = lane >> 1;
@@ -191,9 +226,9 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
 #pragma unroll
                     for (int q = 0; q < kMaxSections; ++q)
                         if (q == k) lk = lcum[q];
-                    const float a = logf(fmaf(num.re, num.re, num.im * num.im)) -
-                                    logf(fmaf(den.re, den.re, den.im * den.im)) +
-                                    logf(fmaxf(1.f, ir2)) - 2.f * lk;
+                    const float a = __logf(fmaf(num.re, num.re, num.im * num.im)) -
+                                    __logf(fmaf(den.re, den.re, den.im * den.im)) +
+                                    __logf(fmaxf(1.f, ir2)) - 2.f * lk;
                     lz2 = fmaxf(lz2, a);
                 }
                 const float ims = 1.f / num_scale(rowsf[k]);
@@ -206,13 +241,13 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
             res = cdiv(num, den);
             const float R = sqrtf(fmaf(num.re, num.re, num.im * num.im) /
                                   fmaf(den.re, den.re, den.im * den.im));
-            lr = logf(r);
+            lr = __logf(r);
             if (R > 0.f) {
-                la = logf(kHorizonEps * (1.f - r) / ((float)np * R));
+                la = __logf(kHorizonEps * (1.f - r) / ((float)np * R));
                 ilr = 1.f / lr;
             }
             // log of the initial-state response bound, before its r^T decay
-            zs = 0.5f * lz2 - logf(1.f - r);
+            zs = 0.5f * lz2 - __logf(1.f - r);
             if (!(fabsf(la) < 1e30f) || !(zs < 1e30f)) bad = true;
         }
     }
@@ -221,15 +256,18 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
     // of the terms' magnitudes beside it (how much the sum cancels)
     if (lane < np) s_res[lane] = res;
     __syncwarp();
+    // (the (j, i) term is the conjugate of the (i, j) one: lane i sums j >= i,
+    // the off-diagonal terms twice)
     float e = 0.f, eabs = 0.f;
     if (lane < np) {
         const cpx pi = s_pole[lane];
-        for (int j = 0; j < np; ++j) {
+        for (int j = lane; j < np; ++j) {
             const cpx pj = s_pole[j], rj = s_res[j];
             const cpx q = cmul(pi, cpx{pj.re, -pj.im});
             const cpx t = cdiv(cmul(cmul(res, cpx{rj.re, -rj.im}), q), cpx{1.f - q.re, -q.im});
-            e += t.re;
-            eabs += cabs_(t);
+            const float w = j == lane ? 1.f : 2.f;
+            e = fmaf(w, t.re, e);
+            eabs = fmaf(w, cabs_(t), eabs);
         }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -248,10 +286,10 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
 // carried.  -1 where no horizon holds.
 __device__ int horizon_combine(bool ok, float h2, int K, int64_t T, int64_t G, float la, float ilr,
                                float zs, float lr, int64_t& seg) {
-    float ptail = ilr != 0.f ? (la + logf(h2)) * ilr : 0.f;
+    float ptail = ilr != 0.f ? (la + __logf(h2)) * ilr : 0.f;
     // the initial state's response (each pole's share counted 2K times) has
     // decayed below the bound after tz samples
-    const float lb = logf(kHorizonEps * h2 / (float)(2 * K));
+    const float lb = __logf(kHorizonEps * h2 / (float)(2 * K));
     float tz = (lr < 0.f && zs > -1e30f) ? (lb - zs) / lr : 0.f;
     for (int o = 16; o > 0; o >>= 1) {
         ptail = fmaxf(ptail, __shfl_xor_sync(0xffffffffu, ptail, o));
@@ -353,6 +391,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     __shared__ float s_rowf[kMaxSections][5];  // the same rows rounded to FP32
     __shared__ double s_G[kMaxSections];
     __shared__ float s_Ginv[kMaxSections];      // 1 / G_k
+    __shared__ float s_dfscan[kMaxSections];    // 1: extended-precision section
     __shared__ double s_b0inv[kMaxSections];    // 1 / b0 (normalised), 0 if b0 = 0
     __shared__ float s_h2;                      // ||h||_2 lower bound
     __shared__ int s_mode, s_horizon, s_err;
@@ -473,7 +512,8 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             else if (P >= 0) nt = (len + seg - 1) / seg;
             else nt = (len + T - 1) / T;
             p.chan[c].horizon = P;
-            p.chan[c].single = single;
+            p.chan[c].single = (int16_t)single;
+            if (Kc == 0) p.chan[c].ext = 0;  // (else written by the first section warp)
             p.chan[c].seg = P >= 0 ? seg : p.seg;
             p.chan[c].ntiles = (int32_t)nt;
             s_horizon = P;
@@ -544,19 +584,36 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
         for (int j = 0; j < 5; ++j)
             if ((lane >> j) & 1) P = dfm_mul(P, s_chain[k][j]);
         out32->lane_pow[lane] = to_f4(P);
+        out32->lane_lo[lane] = to_f4_lo(P);
+        float m = max_entry(P);
+        if (lane < 5) {
+            const dfm2 Q = s_chain[k][lane];
+            out32->phi_pow[lane] = to_f4(Q);
+            out32->phi_lo[lane] = to_f4_lo(Q);
+            m = fmaxf(m, max_entry(Q));
+        }
+        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+        s_dfscan[k] = (m > kDfScanEntry || coef_sensitivity(a1, a2) > kDfCoefSens) ? 1.f : 0.f;
     }
-    if (lane < 5) out32->phi_pow[lane] = to_f4(s_chain[k][lane]);
+    __syncwarp();
     if (lane == 0) {
         // b1 / b0 and b2 / b0 when b0 is factored (1 / b0 from the rows phase)
         const double sb = mode ? s_b0inv[k] : 1.0;
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
-        out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], 0.0f);
+        out32->alo = make_float4((float)(a1 - (double)(float)a1), (float)(a2 - (double)(float)a2),
+                                 0.0f, 0.0f);
+        out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], s_dfscan[k]);
         out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
     }
 
     // ---- Psi = A^(NL) and Theta = A^T, only for channels carried by the
     // look-back (its warp and tile steps) ----
     asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
+    if (k == 0 && lane == 0) {
+        int16_t e = 0;
+        for (int j = 0; j < Kc; ++j) e |= s_dfscan[j] != 0.f ? 1 : 0;
+        p.chan[c].ext = e;
+    }
     if (s_horizon >= 0) return;
     if (lane == 0) {
         dfm2 P = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32

@@ -56,7 +56,8 @@ struct ChanInfo {
     int64_t slot;     // first look-back slot of the channel (ceil(len / T) slots)
     int32_t horizon;  // >= 0: memory horizon P (segments start P samples early, no
                       // carry); -1: the state is carried by the look-back
-    int32_t single;   // 1: the whole channel is one segment (backward plans)
+    int16_t single;   // 1: the whole channel is one segment (backward plans)
+    int16_t ext;      // 1: some section runs in extended precision (Coef32::misc.w)
     int64_t seg;      // segment length of a channel with a horizon (a multiple of 32 N,
                       // at least 2 P)
 };
@@ -88,7 +89,7 @@ constexpr int32_t kFlagBackwardPlan = 1 << 16;
 // stored row-major in a float4 (m00, m01, m10, m11).
 struct __align__(16) Coef32 {
     float4 ab;            // a1, a2, b1, b2  (b1, b2 divided by b0 when factored)
-    float4 misc;          // b0, G_k (cumulative gain), 1/G_k, unused
+    float4 misc;          // b0, G_k (cumulative gain), 1/G_k, 1 if extended precision
     float4 braw;          // b0, b1, b2 normalised by a0 only (the adjoint's FIR)
     float4 phi_pow[5];    // Phi^(2^j), j = 0..4 (lane scan)
     float4 psi_pow[4];    // Psi^(2^r), r = 0..3 (warp scan)
@@ -103,7 +104,23 @@ struct __align__(16) Coef32 {
     float4 cr_d[2];       // d_0 .. d_7
     float4 cr_tpow[5];    // C^(2^j), row-major
     float4 cr_misc;       // e_n, f_n, kappa = max |g_i|, 1 if CR is used for this section
+    // read only by sections that run in extended precision (misc.w): the low
+    // parts of phi_pow and lane_pow (each power = hi + lo in double-float)
+    // and of a1, a2 (alo.x, alo.y; the exact a_i = ab + alo to 48 bits)
+    float4 phi_lo[5];
+    float4 lane_lo[32];
+    float4 alo;
 };
+
+// A section runs in extended precision (misc.w) when the largest entry of
+// its powers Phi^(2^j), Phi^l exceeds kDfScanEntry (poles close to z = +-1
+// near the unit circle: the entries grow to about min(l N, 1 / sin(theta))
+// and the FP32 products of the lane scan cancel), or when rounding a1, a2 to
+// FP32 moves its poles by more than kDfCoefSens of their distance to the
+// circle.  Its lane scan and fold then run in double-float and its in-lane
+// recursions add the coefficients' low parts (two FMAs per sample and pass).
+constexpr float kDfScanEntry = 8.f;
+constexpr double kDfCoefSens = 1e-4;
 
 // Per (channel, section) double-float powers of the tile transition
 // Theta = A^T (T = tile length) for the cross-tile composition, each as

@@ -66,8 +66,9 @@ struct WsCursor {
 // filter this one in registers, store the segment's own outputs.  ZF: the
 // group holding the channel's last sample, whose final state (zf) is taken at
 // element mq of lane `owner`'s chunk; instantiated apart so that the hot
-// loop holds no zf code.
-template <int N, bool FACT, bool CR, bool ZF>
+// loop holds no zf code.  DFS: some section of the channel runs its lane scan
+// in double-float (Coef32::misc.w); instantiated apart for the same reason.
+template <int N, bool FACT, bool CR, bool ZF, bool DFS>
 __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, float* slots,
                                          float2* zs, int lane, int& cur, WsCursor& q, bool last,
                                          bool& pending, const float* nsrc, int64_t nrem,
@@ -108,6 +109,12 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
         if (CR) {
             pipe_section_cr<N, FACT, ZF>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, lane == owner, mq,
                                          row, zf_dst, G);
+        } else if (DFS && cf->misc.w != 0.f) {
+            const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane], alo = cf->alo;
+            pipe_section<N, FACT, ZF, false, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
+                                                          lane == owner, mq, row, zf_dst, G, -1,
+                                                          0.f, 0.f, cf->phi_lo, lpl,
+                                                          make_float2(alo.x, alo.y));
         } else {
             const float4 lp = cf->lane_pow[lane];
             pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
@@ -152,7 +159,7 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
 // slot `cur` holds the segment's first group if `pending`; on exit `cur` is
 // the slot of the next segment's first group, and `pending` says whether it
 // was issued (nsrc: that group's source, nullptr if none).
-template <int N, bool FACT, bool CR>
+template <int N, bool FACT, bool CR, bool DFS>
 __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, float* slots,
                                            float2* zs, int lane, int& cur, bool& pending,
                                            const float* nsrc, int64_t nrem) {
@@ -187,11 +194,11 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
     const bool zf_last = p.zf && sg.out_hi == sg.len;
     const int ghot = zf_last ? ng - 1 : ng;
     for (int g = 0; g < ghot; ++g)
-        ws_group<N, FACT, CR, false>(p, sg, slots, zs, lane, cur, q, g + 1 == ng, pending, nsrc,
+        ws_group<N, FACT, CR, false, DFS>(p, sg, slots, zs, lane, cur, q, g + 1 == ng, pending, nsrc,
                                      nrem, 0, 0);
     if (zf_last) {
         const int rel = (int)(sg.len - 1 - sg.cstart);
-        ws_group<N, FACT, CR, true>(p, sg, slots, zs, lane, cur, q, true, pending, nsrc, nrem,
+        ws_group<N, FACT, CR, true, DFS>(p, sg, slots, zs, lane, cur, q, true, pending, nsrc, nrem,
                                     (rel % WC::kGroup) / N, rel % N);
     }
 }
@@ -243,14 +250,28 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
             bool cr = CRK;
             for (int k = 0; k < sg.K && cr; ++k)
                 cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
+            // PH sections whose lane scan runs in double-float
+            bool dfs = false;
+            for (int k = 0; k < sg.K && !dfs; ++k)
+                dfs = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].misc.w) != 0.f;
             if (CRK && fact && cr)
-                ws_segment<N, true, CRK>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+                ws_segment<N, true, CRK, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
+                                                nrem);
             else if (CRK && cr)
-                ws_segment<N, false, CRK>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+                ws_segment<N, false, CRK, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
+                                                 nrem);
+            else if (fact && dfs)
+                ws_segment<N, true, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
+                                                 nrem);
             else if (fact)
-                ws_segment<N, true, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+                ws_segment<N, true, false, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
+                                                  nrem);
+            else if (dfs)
+                ws_segment<N, false, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
+                                                  nrem);
             else
-                ws_segment<N, false, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
+                ws_segment<N, false, false, false>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                   nsrc, nrem);
         }
         d = dn;
         if (d < total) sg = seg_geom<WC::kGroup>(p, d);

@@ -28,6 +28,11 @@ def test_candidates():
     assert set(c) >= set(h)
     assert all((n, w) in at.SUPPORTED_NW for (n, w, _, _) in c)
     assert len(c) == 2 * sum(len(at.KERNELS[n]) for (n, _) in at.SUPPORTED_NW)
+    # ill-conditioned sections: PH on the warp-segment kernel only
+    e = at.candidates(False, True)
+    assert e and all(a == 1 and not (f & at.SECTION_PIPELINE) for (_, _, a, f) in e)
+    assert set(e) <= set(h)
+    assert at.shape_key([1 << 20], 8, False, True) != at.shape_key([1 << 20], 8, False)
 
 
 def test_cache_file_round_trip(tmp_path, monkeypatch):
