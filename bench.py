@@ -176,7 +176,7 @@ def oracle_baseline(wl, target_seconds: float = 10.0, checks=()):
                                    "samples": 0, "within_tolerance": 0}
             if factor is not None:
                 prev.update({"fp32_sequential_rel_l2": 0.0, "fp32_factor": factor,
-                             "within_fp32_bound": 0})
+                             "within_fp32_bound": 0, "worst_error_over_bound": 0.0})
         prev["rel_l2"] = max(prev["rel_l2"], err)
         prev["channels"] += 1
         prev["samples"] += int(xs.numel())
@@ -190,7 +190,9 @@ def oracle_baseline(wl, target_seconds: float = 10.0, checks=()):
                    else scipy.signal.sosfilt(s32, x32, zi=zi32)[0])
             e32 = float(np.linalg.norm(y32.astype(np.float64) - ref) / nref)
             prev["fp32_sequential_rel_l2"] = max(prev["fp32_sequential_rel_l2"], e32)
-            prev["within_fp32_bound"] += int(err <= max(tol, factor * e32))
+            bound = max(tol, factor * e32)
+            prev["within_fp32_bound"] += int(err <= bound)
+            prev["worst_error_over_bound"] = max(prev["worst_error_over_bound"], err / bound)
     x = wl.x.detach().cpu().double().numpy()
     sos = wl.sos.cpu().numpy()
     K = wl.K.cpu().numpy()

@@ -57,21 +57,26 @@ __device__ __forceinline__ float max_entry(const dfm2& m) {
 // How far rounding a1, a2 to FP32 moves the poles of z^2 + a1 z + a2,
 // relative to their distance from the unit circle: |dp| <= (r |da1| + |da2|)
 // / |p1 - p2| (first order, from p^2 + a1 p + a2 = 0), over 1 - r.
-// Infinite for a double pole or one on or outside the circle.
-__device__ __forceinline__ double coef_sensitivity(double a1, double a2) {
-    const double da1 = a1 - (double)(float)a1, da2 = a2 - (double)(float)a2;
-    const double disc = a1 * a1 - 4.0 * a2;
-    double r, sep;
-    if (disc < 0.0) {
-        r = sqrt(a2);
-        sep = sqrt(-disc);
+// Infinite for a double pole or one on or outside the circle.  The rounding
+// errors, the discriminant and 1 - a2 are formed in FP64 (they cancel), the
+// rest in FP32 (a threshold test; FP64 division and square roots are slow on
+// this part).
+__device__ __forceinline__ float coef_sensitivity(double a1, double a2) {
+    const float da1 = fabsf((float)(a1 - (double)(float)a1));
+    const float da2 = fabsf((float)(a2 - (double)(float)a2));
+    const float disc = (float)fma(a1, a1, -4.0 * a2);
+    float r, sep, gap;
+    if (disc < 0.f) {
+        sep = sqrtf(-disc);
+        r = sqrtf((float)a2);
+        gap = (float)(1.0 - a2) / (1.f + r);  // 1 - r
     } else {
-        sep = sqrt(disc);
-        r = fmax(fabs(-a1 + sep), fabs(-a1 - sep)) * 0.5;
+        sep = sqrtf(disc);
+        r = 0.5f * (fabsf((float)a1) + sep);
+        gap = 1.f - r;
     }
-    const double gap = 1.0 - r;
-    if (!(sep > 0.0) || !(gap > 0.0)) return INFINITY;
-    return (r * fabs(da1) + fabs(da2)) / (sep * gap);
+    if (!(sep > 0.f) || !(gap > 0.f)) return INFINITY;
+    return (r * da1 + da2) / (sep * gap);
 }
 
 __device__ __forceinline__ bool finite_row(const double* r) {
@@ -593,7 +598,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             m = fmaxf(m, max_entry(Q));
         }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        s_dfscan[k] = (m > kDfScanEntry || coef_sensitivity(a1, a2) > kDfCoefSens) ? 1.f : 0.f;
+        s_dfscan[k] = (m > kDfScanEntry || coef_sensitivity(a1, a2) > (float)kDfCoefSens) ? 1.f : 0.f;
     }
     __syncwarp();
     if (lane == 0) {
