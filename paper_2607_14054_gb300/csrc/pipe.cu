@@ -24,6 +24,8 @@
 // slot through.  No warp waits on another's state, only on data, and the
 // permutation in and out is paid once per group for the whole cascade
 // (Sec. VII-B).
+#include <type_traits>
+
 #include "sos_pipe.cuh"
 #include "pipe_section.cuh"
 
@@ -58,66 +60,47 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
     }
     float* zf_dst = p.zf + ((int64_t)sg.c * p.kmax + k) * 2;
     const float G = misc.y;
-    for (int g = 0; g < sg.ngroups; ++g) {
+    // one group; ZG: the group holding the channel's last sample (the last
+    // group of the segment), run after the loop so that the loop's code
+    // holds none of the zf selects
+    auto group = [&](int g, auto zg) {
+        constexpr bool ZG = decltype(zg)::value;
         pipe_wait(p, &sh.bar[s][k], use & 1u, lane);
         float* row = ring + s * SL::kFloats + lane * SL::kRow;
-        const bool zf_owner = g == g_last && lane == owner;
-        if (!CR) {
-            float v[N];
+        const bool zf_owner = ZG && lane == owner;
+        float v[N];
 #pragma unroll
-            for (int q = 0; q < N / 4; ++q) {
-                const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
-                v[4 * q + 0] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
-            if (ZFK && g == g_last)
-                pipe_section<N, FACT, true>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row,
-                                            zf_dst, FACT ? G : 1.f);
-            else
-                pipe_section<N, FACT, false>(v, ab, misc.x, phi, lp, Z1, Z2, false, 0, row,
-                                             zf_dst, 1.f);
-            if (FACT && last_k) {
-#pragma unroll
-                for (int m = 0; m < N; ++m) v[m] *= G;
-            }
-#pragma unroll
-            for (int q = 0; q < N / 4; ++q)
-                *reinterpret_cast<float4*>(row + 4 * q) =
-                    make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-        } else {
-            float v[N];
-#pragma unroll
-            for (int q = 0; q < N / 4; ++q) {
-                const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
-                v[4 * q + 0] = t.x;
-                v[4 * q + 1] = t.y;
-                v[4 * q + 2] = t.z;
-                v[4 * q + 3] = t.w;
-            }
-            if (ZFK && g == g_last)
-                pipe_section_cr<N, FACT, true>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row,
-                                               zf_dst, FACT ? G : 1.f);
-            else
-                pipe_section_cr<N, FACT, false>(v, ab, misc.x, sh.cr[k], Z1, Z2, false, 0, row,
-                                                zf_dst, 1.f);
-            if (FACT && last_k) {
-#pragma unroll
-                for (int m = 0; m < N; ++m) v[m] *= G;
-            }
-#pragma unroll
-            for (int q = 0; q < N / 4; ++q)
-                *reinterpret_cast<float4*>(row + 4 * q) =
-                    make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        for (int q = 0; q < N / 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
+            v[4 * q + 0] = t.x;
+            v[4 * q + 1] = t.y;
+            v[4 * q + 2] = t.z;
+            v[4 * q + 3] = t.w;
         }
+        if (!CR)
+            pipe_section<N, FACT, ZG>(v, ab, misc.x, phi, lp, Z1, Z2, zf_owner, mq, row, zf_dst,
+                                      (ZG && FACT) ? G : 1.f);
+        else
+            pipe_section_cr<N, FACT, ZG>(v, ab, misc.x, sh.cr[k], Z1, Z2, zf_owner, mq, row,
+                                         zf_dst, (ZG && FACT) ? G : 1.f);
+        if (FACT && last_k) {
+#pragma unroll
+            for (int m = 0; m < N; ++m) v[m] *= G;
+        }
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            *reinterpret_cast<float4*>(row + 4 * q) =
+                make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         __syncwarp();
         pipe_arrive(&sh.bar[s][k + 1]);
         if (++s == kPipeRing) {
             s = 0;
             ++use;
         }
-    }
+    };
+    const int nplain = g_last >= 0 ? g_last : sg.ngroups;  // g_last = ngroups - 1 if set
+    for (int g = 0; g < nplain; ++g) group(g, std::false_type{});
+    if (ZFK && g_last >= 0) group(g_last, std::true_type{});
 }
 
 template <int N, bool ZFK>

@@ -582,6 +582,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
 
     Coef32* out32 = p.c32 + ((int64_t)c * kmax + k);
     CoefDF* outdf = p.cdf + ((int64_t)c * kmax + k);
+    float m;  // largest entry of the section's powers (all lanes)
     {
         // Phi^lane by binary powering (exact additions: for poles near the
         // unit circle the entries come out of near-cancelling sums)
@@ -590,7 +591,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             if ((lane >> j) & 1) P = dfm_mul(P, s_chain[k][j]);
         out32->lane_pow[lane] = to_f4(P);
         out32->lane_lo[lane] = to_f4_lo(P);
-        float m = max_entry(P);
+        m = max_entry(P);
         if (lane < 5) {
             const dfm2 Q = s_chain[k][lane];
             out32->phi_pow[lane] = to_f4(Q);
@@ -598,16 +599,18 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             m = fmaxf(m, max_entry(Q));
         }
         for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        s_dfscan[k] = (m > kDfScanEntry || coef_sensitivity(a1, a2) > (float)kDfCoefSens) ? 1.f : 0.f;
     }
-    __syncwarp();
     if (lane == 0) {
+        // extended precision (FP64 work on one lane: the FP64 pipe is narrow)
+        const float ext =
+            (m > kDfScanEntry || coef_sensitivity(a1, a2) > (float)kDfCoefSens) ? 1.f : 0.f;
+        s_dfscan[k] = ext;
         // b1 / b0 and b2 / b0 when b0 is factored (1 / b0 from the rows phase)
         const double sb = mode ? s_b0inv[k] : 1.0;
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
         out32->alo = make_float4((float)(a1 - (double)(float)a1), (float)(a2 - (double)(float)a2),
                                  0.0f, 0.0f);
-        out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], s_dfscan[k]);
+        out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], ext);
         out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
     }
 
