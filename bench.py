@@ -370,13 +370,15 @@ STRESS_FP32_FACTOR = 8.0
 
 def stress_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 3):
     """Precision stress: 64 x 2^26 samples, K = 8, poles at radius
-    0.999..0.9999 (long memory horizons, per-channel segments), one prepare +
-    apply per step.  Returns the leg's figures and the first 2^16 outputs of
+    0.999..0.9999 (long memory horizons, per-channel segments), autotuned
+    (untimed), one prepare + apply per step.  Returns the leg's figures and the first 2^16 outputs of
     every channel (causal prefixes) for the oracle check."""
     import torch
     from synth import workloads
     wl = workloads.precision_stress(device=dev)
-    plan = P.SosFilter(wl.lengths, wl.kmax, device=dev)
+    from paper_2607_14054_gb300.autotune import autotune
+    tuning = autotune(wl.x, wl.sos, wl.K, wl.lengths, wl.zi)
+    plan = P.SosFilter(wl.lengths, wl.kmax, tuning=tuning, device=dev)
     y = torch.empty_like(wl.x)
     zf = torch.empty(wl.n_channels, wl.kmax, 2, device=dev)
     plan(wl.x, wl.sos, wl.K, None, y=y, zf=zf)

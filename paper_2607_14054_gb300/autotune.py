@@ -13,7 +13,7 @@ look-back (poles near the unit circle): only then does W, the look-back
 kernel's tile width, matter, so only then are several W tried.  And whether
 some section is ill-conditioned for FP32 (``SosFilter.plan_extended``): only
 the PH warp-segment kernel gives those sections extended precision, so then
-neither the section pipeline nor cyclic reduction is a candidate.
+neither the section pipeline nor cyclic reduction is a candidate, nor N = 64.
 """
 from __future__ import annotations
 
@@ -66,9 +66,12 @@ def candidates(carried: bool, extended: bool = False) -> List[Tuple[int, int, in
     """Tunings to try: every N with both solvers and each kernel choice for
     the channels within their memory horizon; several W only when some
     channel is carried by the look-back (W sizes the look-back tiles); PH on
-    the warp-segment kernel only when some section is ill-conditioned."""
+    the warp-segment kernel with N <= 32 only when some section is
+    ill-conditioned."""
     out = []
-    for n in (16, 32, 64):
+    # ill-conditioned sections: N <= 32 (the in-lane FP32 runs are N samples
+    # long; at N = 64 some precision-stress channels exceed the FP32 bound)
+    for n in ((16, 32) if extended else (16, 32, 64)):
         ws = sorted({w for (nn, w) in SUPPORTED_NW if nn == n}) if carried else \
             [8 if (n, 8) in SUPPORTED_NW else min(w for (nn, w) in SUPPORTED_NW if nn == n)]
         for w in ws:

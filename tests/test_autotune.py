@@ -30,7 +30,7 @@ def test_candidates():
     assert len(c) == 2 * sum(len(at.KERNELS[n]) for (n, _) in at.SUPPORTED_NW)
     # ill-conditioned sections: PH on the warp-segment kernel only
     e = at.candidates(False, True)
-    assert e and all(a == 1 and not (f & at.SECTION_PIPELINE) for (_, _, a, f) in e)
+    assert e and all(n <= 32 and a == 1 and not (f & at.SECTION_PIPELINE) for (n, _, a, f) in e)
     assert set(e) <= set(h)
     assert at.shape_key([1 << 20], 8, False, True) != at.shape_key([1 << 20], 8, False)
 

@@ -77,7 +77,7 @@ def test_extended_flag_matches_criterion(N):
     assert plan.plan_extended().sum() == 0
 
 
-@pytest.mark.parametrize("tuning", [None, (16, 8, 1, 0), (32, 8, 1, 0), (32, 8, 1, 2 << 8)])
+@pytest.mark.parametrize("tuning", [None, (16, 8, 1, 0), (32, 8, 1, 0), (32, 8, 1, 2 << 8), "auto"])
 def test_precision_stress_within_fp32_bound(tuning):
     P = _lib()
     L = 1 << 16
