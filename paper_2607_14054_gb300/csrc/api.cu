@@ -236,10 +236,13 @@ sos_status apply_parts(const float* x, int32_t n_channels, int32_t kmax,
     if (total > 0 && (parts & kPartPipe)) {
         const int64_t sms = device_sms() > 0 ? device_sms() : 1;
         cudaError_t e;
+        // launched early (programmatic dependent launch): its CTAs become
+        // resident while the preceding kernel (normally the plan) finishes,
+        // and wait for that kernel's completion on the device
         if (p.flags_opt & SOS_FLAG_SECTION_PIPELINE)
-            e = launch_pipe(p, sms * kPipeCtasPerSm, st, false);
+            e = launch_pipe(p, sms * kPipeCtasPerSm, st, true);
         else
-            e = launch_warpseg(p, sms * warpseg_ctas(p.N, p.algo, p.flags_opt), st, false);
+            e = launch_warpseg(p, sms * warpseg_ctas(p.N, p.algo, p.flags_opt), st, true);
         if (e != cudaSuccess) return SOS_ERR_CUDA;
         early = true;
     }

@@ -110,6 +110,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     // the look-back kernel queued behind this one may be launched now (it
     // waits for this kernel's completion before it starts work)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // launched early behind the plan kernel: wait for its completion (and
+    // its writes) before the first read of the plan's tables
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ float4 s_ring4[];
     float* ring = reinterpret_cast<float*>(s_ring4);
     __shared__ PipeShared sh;

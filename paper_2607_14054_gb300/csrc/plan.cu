@@ -822,6 +822,10 @@ namespace sosf {
 // channel table.  The last block to finish then builds the dispatch order
 // (order_pass), so that a call's set-up is a single launch.
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
+    // the filtering kernel queued behind this one may be launched once every
+    // CTA of the plan has started (it waits for the plan's completion before
+    // it reads anything the plan writes)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ unsigned long long s_key[];
     __shared__ int s_last;
     if ((int)blockIdx.x == p.C) plan_table(p);

@@ -211,6 +211,9 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
     // the look-back kernel queued behind this one may be launched now (it
     // waits for this kernel's completion before it starts work)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // launched early behind the plan kernel: wait for its completion (and
+    // its writes) before the first read of the plan's tables
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ float4 s_ws4[];
     __shared__ float2 s_z[kWsWarps][kMaxSections];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;

@@ -61,7 +61,8 @@ def test_autotuned_call_matches_oracle():
     wl = workloads.batched(n_channels=24, max_len=1 << 16, device="cuda")
     rep = []
     tu = at.autotune(wl.x, wl.sos, wl.K, wl.lengths, wl.zi, report=rep)
-    assert tu in [c for c, _ in rep] and len(rep) >= 6
+    # (the smallest candidate set: a plan with ill-conditioned sections)
+    assert tu in [c for c, _ in rep] and len(rep) >= len(at.candidates(False, True))
     y, zf = P.sosfilt(wl.x, wl.sos, wl.K, wl.lengths, wl.zi, tuning="auto", check=True)
     y_ref, _ = oracle.sosfilt(wl.x.double().cpu().numpy(), wl.sos.cpu().numpy(),
                               K=wl.K.cpu().numpy(), lengths=wl.lengths.numpy(),
