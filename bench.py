@@ -4,11 +4,12 @@
 One step = one full call of the C ABI's sos_filter on the 16th-order (K = 8)
 Butterworth band-pass workload, 2^24 FP32 samples i.i.d. N(0, 1), one
 channel, zero initial state, inputs resident in HBM: sos_prepare (plan and
-dispatch order, one kernel) then sos_apply (the look-back kernel, which finds
-no carried channel here, and the kernel for channels within their memory
-horizon -- warp segments by default, or the section pipeline -- launched early
-behind it).  The tuning (N, W, solver, kernel) is chosen by the library's
-autotuner before the timed region.
+dispatch order, one kernel) then sos_apply (the kernel for channels within
+their memory horizon -- warp segments or the section pipeline -- launched
+early behind the plan, then the look-back kernel, which finds no carried
+channel here, launched early behind that), replayed as one CUDA graph.  The
+tuning (N, W, solver, kernel) is chosen by the library's autotuner before the
+timed region.
 Prints one JSON line (rank 0), with the batched (4096 channels),
 differentiation (forward + backward, 256 x 2^16) and precision-stress
 (64 x 2^26, poles at radius 0.999..0.9999) workloads as extra fields.
