@@ -460,6 +460,8 @@ def main():
     ap.add_argument("--clocks-out", default="")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the batched and differentiation legs")
+    ap.add_argument("--leg", default="", choices=["", "backward"],
+                    help="run only this extra leg and print its figures (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -472,6 +474,12 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2607_14054_gb300 as P
     from synth import workloads
+
+    if args.leg == "backward":
+        line = {"leg": "backward", **backward_leg(P, dev, world, steps=args.steps)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return 0
 
     wl = workloads.plain_bandpass16(n=1 << 24, device=dev)
     Kmax = wl.kmax

@@ -416,18 +416,33 @@ BwdLayout bwd_layout(size_t base, int32_t C, int32_t kmax, int64_t total_len, in
     return L;
 }
 
-// Backward segment length: the call's samples over the adjoint kernel's
-// resident warps, in whole groups (at least 8, at most 64), so that every
-// warp gets about one segment and a horizon of up to half a segment fits.
-int64_t backward_segment_length(int64_t total_len, int N) {
+// Backward segment length, in whole groups (at least 8, at most 64): from
+// the call's samples over the adjoint kernel's resident warps upwards, the
+// length whose segments (whole channels cut at it) take the fewest group
+// steps on the warps, rounds x groups per segment, so that a channel's last
+// partial segment does not start a second round on a few warps; a horizon
+// of up to half a segment fits.
+int64_t backward_segment_length(const int64_t* lengths_host, int32_t C, int64_t total_len,
+                                int N) {
     const int64_t group = 32LL * N;
     const int sms = device_sms() > 0 ? device_sms() : 148;
     int64_t units = adjoint_warps(N, sms);
     if (units < 1) units = 1;
-    int64_t g = (total_len + units * group - 1) / (units * group);
-    if (g < 8) g = 8;
-    if (g > 64) g = 64;
-    return g * group;
+    int64_t g0 = (total_len + units * group - 1) / (units * group);
+    if (g0 < 8) g0 = 8;
+    if (g0 > 64) g0 = 64;
+    int64_t best = g0, best_cost = -1;
+    for (int64_t g = g0; g <= 64 && g <= 2 * g0; ++g) {
+        const int64_t seg = g * group;
+        int64_t nseg = 0;
+        for (int32_t c = 0; c < C; ++c) nseg += (lengths_host[c] + seg - 1) / seg;
+        const int64_t cost = (nseg + units - 1) / units * g;
+        if (best_cost < 0 || cost < best_cost) {
+            best = g;
+            best_cost = cost;
+        }
+    }
+    return best * group;
 }
 
 }  // namespace
@@ -469,7 +484,7 @@ sos_status sos_filter_backward(const float* x, const double* sos, const int32_t*
     // the backward plan: no look-back (a channel without a memory horizon is
     // one segment), segments sized for the adjoint kernel's warps
     p.flags_opt |= kFlagBackwardPlan;
-    p.seg = backward_segment_length(total, p.N);
+    p.seg = backward_segment_length(lengths_host, n_channels, total, p.N);
     p.ck = reinterpret_cast<float*>(ws + BL.ck);
     p.gacc = reinterpret_cast<double*>(ws + BL.gacc);
     if (launch_plan(p, sm) != cudaSuccess) return SOS_ERR_CUDA;
