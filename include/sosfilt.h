@@ -154,7 +154,11 @@ sos_status sos_filter(const float *x, const double *sos, const int32_t *K, int32
 
 /* The two halves of sos_filter, for callers that filter many signals with
  * the same coefficients, section counts and lengths (or that time the
- * filtering kernel alone).
+ * filtering kernel alone).  sos_apply's kernels are launched with
+ * programmatic dependent launch: each may become resident before the kernel
+ * ahead of it in the stream has finished, and waits on the device for that
+ * kernel's completion (and its memory writes) before it reads anything, so
+ * stream order holds as for ordinary launches.
  *
  * sos_prepare enqueues the plan kernel: the per-channel offsets and tile
  * prefix, and the coefficient tables (normalisation by a0, the split-off
