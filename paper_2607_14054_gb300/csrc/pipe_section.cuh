@@ -22,7 +22,7 @@ __device__ __forceinline__ void pick_pair(const float (&v)[N], int mq, float& q0
     }
 }
 
-// Chunk v[] <-> the lane's row, around section_zf_row.
+// Chunk v[] <-> the lane's row (N floats, 16-byte aligned).
 template <int N>
 __device__ __forceinline__ void chunk_to_row(const float (&v)[N], float* row) {
 #pragma unroll
@@ -55,13 +55,11 @@ __device__ __forceinline__ void row_to_chunk(float (&v)[N], const float* row) {
 // of the group start (the inputs before it being zero): added to the
 // all-pole input at pinj and pinj + 1 (the backward's recompute of a
 // channel's first group, whose grid is anchored elsewhere).
-// NOFIR: the all-pole part alone (b0 = 1, b1 = b2 = 0): S3 is skipped.
 // DFS: extended precision for ill-conditioned sections: the lane scan and the
 // fold run in double-float, with the powers' low parts phi_lo and lpl beside
 // phi and lp, and the in-lane recursions add the low parts alo of a1, a2
 // (the samples stay FP32).
-template <int N, bool FACT, bool ZF = false, bool INJ = false, bool NOFIR = false,
-          bool DFS = false>
+template <int N, bool FACT, bool ZF = false, bool INJ = false, bool DFS = false>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
@@ -90,14 +88,12 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
     if (ZF) pick_pair<N>(v, mq, xq, xqm1);
 
     // S3: non-recursive stage with zero history inside the lane
-    const float xl1 = NOFIR ? 0.f : v[N - 1], xl2 = NOFIR ? 0.f : v[N - 2];
-    if (!NOFIR) {
+    const float xl1 = v[N - 1], xl2 = v[N - 2];
 #pragma unroll
-        for (int m = N - 1; m >= 2; --m)
-            v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
-        v[1] = fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]);
-        if (!FACT) v[0] = b0 * v[0];
-    }
+    for (int m = N - 1; m >= 2; --m)
+        v[m] = fmaf(b2, v[m - 2], fmaf(b1, v[m - 1], FACT ? v[m] : b0 * v[m]));
+    v[1] = fmaf(b1, v[0], FACT ? v[1] : b0 * v[1]);
+    if (!FACT) v[0] = b0 * v[0];
     if (INJ) {
 #pragma unroll
         for (int m = 0; m < N; ++m) {
@@ -419,34 +415,5 @@ __device__ __forceinline__ void pipe_section_dual(float (&l)[N], float (&u)[N], 
     U2 = __shfl_sync(0xffffffffu, uo2, 31);
 }
 
-// The group holding the channel's last sample, out of line: the lane chunk
-// travels through the lane's shared-memory row (row[0, N)), so the registers
-// the run-time zf indexing needs are not reserved by the callers' hot loops.
-// coef: Phi^(2^j) (PH) or the cyclic-reduction coefficients (CR).  Returns
-// the group's outgoing state.
-template <int N, bool FACT, bool CR>
-__device__ __noinline__ float2 section_zf_row(float* row, const float4 ab, const float b0,
-                                              const float4* coef, const float4 lp, float2 z,
-                                              bool zf_owner, int mq, float* zf_dst, float G) {
-    float v[N];
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q) {
-        const float4 t = *reinterpret_cast<const float4*>(row + 4 * q);
-        v[4 * q + 0] = t.x;
-        v[4 * q + 1] = t.y;
-        v[4 * q + 2] = t.z;
-        v[4 * q + 3] = t.w;
-    }
-    if (CR)
-        pipe_section_cr<N, FACT, true>(v, ab, b0, coef, z.x, z.y, zf_owner, mq, row, zf_dst, G);
-    else
-        pipe_section<N, FACT, true>(v, ab, b0, coef, lp, z.x, z.y, zf_owner, mq, row, zf_dst, G);
-#pragma unroll
-    for (int q = 0; q < N / 4; ++q)
-        *reinterpret_cast<float4*>(row + 4 * q) =
-            make_float4(v[4 * q + 0], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
-    __syncwarp();
-    return z;
-}
 
 }  // namespace sosf

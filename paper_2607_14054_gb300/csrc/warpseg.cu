@@ -111,10 +111,10 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
                                          row, zf_dst, G);
         } else if (DFS && cf->misc.w != 0.f) {
             const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane], alo = cf->alo;
-            pipe_section<N, FACT, ZF, false, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
-                                                          lane == owner, mq, row, zf_dst, G, -1,
-                                                          0.f, 0.f, cf->phi_lo, lpl,
-                                                          make_float2(alo.x, alo.y));
+            pipe_section<N, FACT, ZF, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
+                                                   lane == owner, mq, row, zf_dst, G, -1, 0.f,
+                                                   0.f, cf->phi_lo, lpl,
+                                                   make_float2(alo.x, alo.y));
         } else {
             const float4 lp = cf->lane_pow[lane];
             pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
