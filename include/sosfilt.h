@@ -89,8 +89,11 @@ typedef enum sos_status {
  *             instead of the default warp-segment kernel (one warp filters a
  *             whole segment through all K sections, segments sized to give
  *             every resident warp work).  Segment lengths differ, so the same
- *             flags must reach sos_prepare and sos_apply.  The backward always
- *             runs the section pipeline.
+ *             flags must reach sos_prepare and sos_apply.  Every section runs
+ *             in FP32 there: sections flagged as ill-conditioned
+ *             (sos_plan_extended) get extended precision only on the
+ *             warp-segment kernel.  The backward runs its own adjoint kernel
+ *             whatever this bit.
  *             bits 8..11 (SOS_FLAG_WS_CTAS(n)): CTAs per SM of the
  *             warp-segment launch, 1..15 (0 = as many as fit; more than fit
  *             is clamped).  Fewer, longer-running warps suit calls whose
