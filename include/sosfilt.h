@@ -94,6 +94,14 @@ typedef enum sos_status {
  *             (sos_plan_extended) get extended precision only on the
  *             warp-segment kernel.  The backward runs its own adjoint kernel
  *             whatever this bit.
+ *             bit 3 (SOS_FLAG_REPLAN): recompute every channel's tables in
+ *             sos_prepare even where the plan cache would keep them (see
+ *             sos_prepare; same results, for timing the full plan).
+ *             bit 4 (SOS_FLAG_DOUBLE_FLOAT): run every channel within its
+ *             memory horizon with double-float samples (precision class 3
+ *             of sos_plan_extended), whatever the plan's estimate; about ten
+ *             times the arithmetic, for results within about 2^-40 of the
+ *             exact ones where FP32 would lose digits.
  *             bits 8..11 (SOS_FLAG_WS_CTAS(n)): CTAs per SM of the
  *             warp-segment launch, 1..15 (0 = as many as fit; more than fit
  *             is clamped).  Fewer, longer-running warps suit calls whose
@@ -121,6 +129,8 @@ typedef struct sos_tuning {
 #define SOS_FLAG_CHECK_STABLE 1
 #define SOS_FLAG_CARRY_ONLY 2
 #define SOS_FLAG_SECTION_PIPELINE 4
+#define SOS_FLAG_REPLAN 8
+#define SOS_FLAG_DOUBLE_FLOAT 16
 #define SOS_FLAG_WS_CTAS(n) (((n) & 15) << 8)
 #define SOS_MAX_SECTIONS 8
 
@@ -167,7 +177,14 @@ sos_status sos_filter(const float *x, const double *sos, const int32_t *K, int32
  * prefix, and the coefficient tables (normalisation by a0, the split-off
  * gain of Sec. II, Eq. simple_second_order, and the transition-matrix powers,
  * "pre-computed before filtering" as in Sec. VI-B, formed in FP64).  It also
- * clears the workspace's device status word.
+ * clears the workspace's device status word.  Plan cache: the workspace
+ * keeps, per channel, the raw sos rows (bit for bit), K and length its tables
+ * were built from, and the call-level inputs (tuning, kmax, channel count);
+ * a channel whose inputs all match keeps its tables and the plan kernel skips
+ * it on the device (no host synchronisation), and when every channel matches
+ * the dispatch order is kept too.  Changing any coefficient, K, length or
+ * tuning recomputes what depends on it.  SOS_FLAG_REPLAN turns the cache off
+ * for a call.  sos_plan_recomputed() reports what the latest plan did.
  *
  * sos_apply enqueues only the filtering kernel, reusing those tables; it may
  * be called any number of times after one sos_prepare on the same workspace
@@ -210,16 +227,20 @@ sos_status sos_apply_carried(const float *x, int32_t n_channels, int32_t kmax,
  * device memory (held by every GPU that loads the library until the process
  * exits).  The caller still provides x, sos, K, lengths, zi, y and zf exactly
  * as for sos_filter.
- *   - The first call on a device looks up the array's device address and
- *     zeroes it (a synchronous cudaMemset); make that first call before any
- *     stream capture.  It allocates nothing and calls no allocating routine.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address and zeroes it on `stream`, then waits for
+ *     `stream` so that the zeroing has finished before any later call on any
+ *     stream; make that first call before any stream capture (during a
+ *     capture it returns SOS_ERR_ARG).  It allocates nothing and calls no
+ *     allocating routine.
  *   - Sizes whose workspace (sos_workspace_size) exceeds 8 MiB are rejected
  *     with SOS_ERR_WORKSPACE; nothing is enqueued.
  *   - Every call shares the one array and leaves its contents behind; calls
  *     that overlap on the GPU (different streams without ordering, or other
  *     host threads) race with each other and give wrong results.
  *   - device_status: NULL, or a host int32 that receives the device-side
- *     status of this call; passing it makes the call wait for `stream`.
+ *     status of this call; passing it makes the call wait for `stream`, so it
+ *     must be NULL while `stream` is being captured (else SOS_ERR_ARG).
  * Returns SOS_OK once the work is enqueued (and, with device_status, done). */
 sos_status sos_filter_static(const float *x, const double *sos, const int32_t *K,
                              int32_t n_channels, int32_t kmax, const int64_t *lengths,
@@ -230,9 +251,13 @@ sos_status sos_filter_static(const float *x, const double *sos, const int32_t *K
  * of the most recent call that used this workspace. */
 sos_status sos_device_status(void *workspace, void *stream);
 
-/* Bytes of device workspace for sos_filter_backward with these sizes (the
- * forward workspace plus kmax * sum(lengths) floats for the section outputs
- * and 5 doubles per section for the coefficient sums).  0 if invalid. */
+/* Bytes of device workspace for sos_filter_backward with these sizes: the
+ * forward workspace, then the forward-state checkpoints of the adjoint
+ * kernel (each section's DF2T state at the start of every group of 32 N
+ * samples, two slots per group so that neighbouring segments of a channel
+ * never share one: 2 * kmax floats per slot) and 5 doubles per (channel,
+ * section) for the coefficient sums.  No per-section signal is stored.
+ * 0 if invalid. */
 size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64_t *lengths_host,
                                    const sos_tuning *tuning);
 
@@ -248,7 +273,10 @@ size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64
  * a2 lambda_{n+2} started from dL/dzf, then dL/du = b0 lambda_n +
  * b1 lambda_{n+1} + b2 lambda_{n+2}; dL/db_j = sum lambda_{n+j} u_n,
  * dL/da_j = -sum lambda_{n+j} y_n, dL/dzi = (lambda_0, lambda_1).  The
- * section outputs are recomputed by a forward pass into the workspace.
+ * section signals are not stored: a forward pass over each segment keeps only
+ * the section states at group starts (checkpoints, in the workspace), and the
+ * adjoint pass recomputes each group's section inputs from its checkpoint in
+ * shared memory just before running that group backwards.
  * Channels without a memory horizon run as one segment each (correct, but
  * without parallelism inside the channel).  Asynchronous on `stream`;
  * argument errors are returned at once, device errors go to the status word. */
@@ -271,19 +299,37 @@ sos_status sos_plan_query(void *workspace, int32_t first, int32_t count, int32_t
                           int32_t *tiles, void *stream);
 
 /* Waits for `stream`, then writes for channels [first, first + count) of the
- * most recent sos_prepare on this workspace whether some section of the
- * channel is ill-conditioned for FP32 (1) or not (0), into extended[i] (a
- * host array of `count` entries).  A section is, when the largest entry of
- * its transition powers A^(N 2^j), A^(N l) exceeds 8 (a pole pair close to
- * z = 1 or z = -1 near the unit circle): the default warp-segment kernel
- * then runs that section's lane scan and fold (S4) in double-float and adds
- * the low parts of a1, a2 in its in-lane recursions; the section pipeline
+ * most recent sos_prepare on this workspace its precision class into
+ * extended[i] (a host array of `count` entries).  The bulk of the method runs
+ * in FP32 with FP64-accurate transition powers (Sec. VI-B); where the plan
+ * finds that FP32 would lose digits it adds precision, and reports how:
+ *   0  every section in FP32;
+ *   1  some section's in-lane recursions add the low parts of a1, a2 (FP32
+ *      rounding of a1, a2 displaces its poles by more than 2^-18 of their
+ *      distance to the unit circle);
+ *   2  some section also runs its lane scan and fold (S4) in double-float
+ *      (the largest entry of its transition powers A^(N 2^j), A^(N l) exceeds
+ *      8, or the displacement exceeds 1e-4);
+ *   3  the whole cascade runs with double-float samples (about 44 bits): the
+ *      plan's estimate of the error that FP32 rounding of the signals handed
+ *      between sections would cause at the output (white input, from the
+ *      norms of the partial cascades by partial fractions) or of a section's
+ *      own rounding (its condition number ||g|| ||b|| / ||h||) exceeds 2^-17,
+ *      or SOS_FLAG_DOUBLE_FLOAT was given.
+ * Classes 1..3 take effect on the warp-segment kernel (the default for
+ * channels within their memory horizon); the section pipeline
  * (SOS_FLAG_SECTION_PIPELINE), the cyclic-reduction solver and the look-back
- * kernel run every section in FP32.  No allocation.  SOS_ERR_ARG if the range
- * is outside the channels of that call or `extended` is NULL.  This query
- * has no counterpart in the paper. */
+ * kernel run every section in FP32.  No allocation.  SOS_ERR_ARG if the
+ * range is outside the channels of that call or `extended` is NULL.  This
+ * query has no counterpart in the paper. */
 sos_status sos_plan_extended(void *workspace, int32_t first, int32_t count, int32_t *extended,
                              void *stream);
+
+/* Waits for `stream`, then writes into *channels the number of channels
+ * whose tables the most recent sos_prepare on this workspace recomputed (0:
+ * every channel's tables and the dispatch order came from the plan cache;
+ * see sos_prepare).  No allocation.  No counterpart in the paper. */
+sos_status sos_plan_recomputed(void *workspace, int32_t *channels, void *stream);
 
 /* Human-readable name of a status code (static string). */
 const char *sos_status_str(sos_status status);

@@ -191,6 +191,15 @@ class SosFilter:
             raise SosError(st, "sos_plan_extended")
         return e
 
+    def plan_recomputed(self) -> int:
+        """Channels whose tables the latest prepare() recomputed (0: all came
+        from the plan cache); synchronises the current stream."""
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st, n = _abi.sos_plan_recomputed(self.workspace.data_ptr(), stream)
+        if st != 0:
+            raise SosError(st, "sos_plan_recomputed")
+        return n
+
     def apply_part(self, part: str, x: torch.Tensor, y: torch.Tensor,
                    zi: Optional[torch.Tensor] = None, zf: Optional[torch.Tensor] = None):
         """One of the two launches of apply(): "pipeline" or "carried"."""

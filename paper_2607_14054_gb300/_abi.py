@@ -20,6 +20,8 @@ SOS_OK = 0
 SOS_FLAG_CHECK_STABLE = 1
 SOS_FLAG_CARRY_ONLY = 2
 SOS_FLAG_SECTION_PIPELINE = 4
+SOS_FLAG_REPLAN = 8
+SOS_FLAG_DOUBLE_FLOAT = 16
 
 
 def SOS_FLAG_WS_CTAS(n: int) -> int:  # noqa: N802 - the C macro's name
@@ -97,6 +99,8 @@ def load(build_if_missing: bool = False):
         lib.sos_plan_query.restype = ctypes.c_int
         lib.sos_plan_extended.argtypes = [vp, i32, i32, vp, vp]
         lib.sos_plan_extended.restype = ctypes.c_int
+        lib.sos_plan_recomputed.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
+        lib.sos_plan_recomputed.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -197,6 +201,14 @@ def sos_plan_extended(ws_ptr: int, first: int, count: int, extended_ptr: int,
     """Host pointer as an integer."""
     V = ctypes.c_void_p
     return int(load().sos_plan_extended(V(ws_ptr), first, count, V(extended_ptr), V(stream)))
+
+
+def sos_plan_recomputed(ws_ptr: int, stream: int):
+    """Returns (status, channels recomputed by the latest plan)."""
+    n = ctypes.c_int32(0)
+    st = int(load().sos_plan_recomputed(ctypes.c_void_p(ws_ptr), ctypes.byref(n),
+                                        ctypes.c_void_p(stream)))
+    return st, int(n.value)
 
 
 def sos_status_str(status: int) -> str:

@@ -163,6 +163,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->rp = reinterpret_cast<int64_t*>(ws + L.rp);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
     p->cdf = reinterpret_cast<CoefDF*>(ws + L.cdf);
+    p->key = reinterpret_cast<unsigned char*>(ws + L.key);
     p->words = reinterpret_cast<unsigned long long*>(ws + L.slots);
     p->cap_tiles = tiles;
     p->C = n_channels;
@@ -381,6 +382,17 @@ sos_status sos_plan_extended(void* workspace, int32_t first, int32_t count, int3
             return SOS_ERR_CUDA;
         for (int32_t i = 0; i < n; ++i) extended[c0 + i] = buf[i].ext;
     }
+    return SOS_OK;
+}
+
+sos_status sos_plan_recomputed(void* workspace, int32_t* channels, void* stream) {
+    if (!workspace || !channels) return SOS_ERR_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    WsHeader h;
+    if (cudaMemcpy(&h, workspace, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    *channels = h.last_recomputed;
     return SOS_OK;
 }
 

@@ -59,7 +59,9 @@ __device__ __forceinline__ void row_to_chunk(float (&v)[N], const float* row) {
 // fold run in double-float, with the powers' low parts phi_lo and lpl beside
 // phi and lp, and the in-lane recursions add the low parts alo of a1, a2
 // (the samples stay FP32).
-template <int N, bool FACT, bool ZF = false, bool INJ = false, bool DFS = false>
+// AL: the in-lane recursions add the low parts alo of a1, a2 (a section
+// whose poles FP32 coefficients would displace noticeably; implied by DFS).
+template <int N, bool FACT, bool ZF = false, bool INJ = false, bool DFS = false, bool AL = DFS>
 __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, const float b0,
                                              const float4* phi, const float4 lp, float& Z1,
                                              float& Z2, bool zf_owner, int mq, float* s_own,
@@ -70,17 +72,17 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
                                              float2 alo = {0.f, 0.f}) {
     const int lane = threadIdx.x & 31;
     const float a1 = ab.x, a2 = ab.y, b1 = ab.z, b2 = ab.w;
-    // the all-pole terms, with a_i = ab + alo for DFS (the low-part products
+    // the all-pole terms, with a_i = ab + alo for AL (the low-part products
     // go first, into the smaller terms), FP32 a_i otherwise:
     // ap2 = t - a1 y1 - a2 y2, ap1 = t - a1 y1, st2 = -a1 y1 - a2 y2, st1 = -a2 y
     auto ap2 = [&](float y1, float y2, float t) {
-        return fmaf(-a1, y1, fmaf(-a2, y2, DFS ? fmaf(-alo.x, y1, fmaf(-alo.y, y2, t)) : t));
+        return fmaf(-a1, y1, fmaf(-a2, y2, AL ? fmaf(-alo.x, y1, fmaf(-alo.y, y2, t)) : t));
     };
-    auto ap1 = [&](float y1, float t) { return fmaf(-a1, y1, DFS ? fmaf(-alo.x, y1, t) : t); };
+    auto ap1 = [&](float y1, float t) { return fmaf(-a1, y1, AL ? fmaf(-alo.x, y1, t) : t); };
     auto st2 = [&](float y1, float y2) {
-        return fmaf(-a1, y1, DFS ? fmaf(-a2, y2, fmaf(-alo.x, y1, -alo.y * y2)) : -a2 * y2);
+        return fmaf(-a1, y1, AL ? fmaf(-a2, y2, fmaf(-alo.x, y1, -alo.y * y2)) : -a2 * y2);
     };
-    auto st1 = [&](float y) { return DFS ? fmaf(-a2, y, -alo.y * y) : -a2 * y; };
+    auto st1 = [&](float y) { return AL ? fmaf(-a2, y, -alo.y * y) : -a2 * y; };
 
     // S8 support: the section input at the channel's last sample (element mq
     // of the owner's chunk), picked by compile-time-indexed selects
@@ -193,6 +195,126 @@ __device__ __forceinline__ void pipe_section(float (&v)[N], const float4 ab, con
         if (zf_owner) {
             zf_dst[0] = f1 * G;
             zf_dst[1] = f2 * G;
+        }
+    }
+}
+
+// Coefficients of one section in double-float, for channels run in extended
+// precision throughout (normalised by a0, never factored).
+struct SecDF {
+    df a1, a2, b0, b1, b2;
+};
+
+// One section over one group with the samples themselves in double-float
+// (chunk vh[] + vl[]): the same steps as pipe_section -- S3 with zero in-lane
+// history, S4 (i) the particular solution's terminal pair, (ii) the lane scan
+// and the fold of the group's incoming state, (iii) the re-run from the true
+// lane state, the group's outgoing state, S8 -- every one in double-float
+// (about 44 bits), so that neither the samples handed from section to section
+// nor the recursions' own roundings are limited to FP32.  For cascades in
+// which later sections attenuate what earlier ones pass (poles next to the
+// unit circle), where FP32 rounding of an intermediate signal reaches the
+// output amplified many times.  Z1, Z2: the group's incoming DF2T state, left
+// outgoing.  ZF: the group holds the channel's last sample (element mq of the
+// chunk of the lane where zf_owner is set), whose state goes to zf_dst.
+template <int N, bool ZF = false>
+__device__ __forceinline__ void pipe_section_dfx(float (&vh)[N], float (&vl)[N], const SecDF& q,
+                                                 const float4* phi, const float4* phi_lo,
+                                                 const float4 lp, const float4 lpl, df& Z1,
+                                                 df& Z2, bool zf_owner, int mq, float* zf_dst) {
+    const int lane = threadIdx.x & 31;
+    const df na1 = df_neg(q.a1);
+    df xq{0.f, 0.f}, xqm1{0.f, 0.f};
+    if (ZF) {
+        pick_pair<N>(vh, mq, xq.hi, xqm1.hi);
+        pick_pair<N>(vl, mq, xq.lo, xqm1.lo);
+    }
+    const df xl1{vh[N - 1], vl[N - 1]}, xl2{vh[N - 2], vl[N - 2]};
+    // S3, top down so that each step still sees the inputs it needs
+#pragma unroll
+    for (int m = N - 1; m >= 2; --m) {
+        const df u = df_dot3(q.b0, df{vh[m], vl[m]}, q.b1, df{vh[m - 1], vl[m - 1]}, q.b2,
+                             df{vh[m - 2], vl[m - 2]});
+        vh[m] = u.hi;
+        vl[m] = u.lo;
+    }
+    {
+        const df u1 = df_dot3(q.b0, df{vh[1], vl[1]}, q.b1, df{vh[0], vl[0]}, df{0.f, 0.f},
+                              df{0.f, 0.f});
+        const df u0 = df_mul(q.b0, df{vh[0], vl[0]});
+        vh[1] = u1.hi;
+        vl[1] = u1.lo;
+        vh[0] = u0.hi;
+        vl[0] = u0.lo;
+    }
+    // S4 (i): the particular solution from zero state, its terminal pair
+    df w0{vh[0], vl[0]};
+    df w1 = df_rec1(df{vh[1], vl[1]}, q.a1, w0);
+#pragma unroll
+    for (int m = 2; m < N; ++m) {
+        const df w2 = df_rec(df{vh[m], vl[m]}, q.a1, w1, q.a2, w0);
+        w0 = w1;
+        w1 = w2;
+    }
+    df s1 = df_rec1(df_dot3(q.b1, xl1, q.b2, xl2, na1, w1), q.a2, w0);
+    df s2 = df_rec1(df_mul(q.b2, xl1), q.a2, w1);
+    // S4 (ii): lane scan, z_{l+1} = Phi z_l + s_l, in double-float
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int d = 1 << j;
+        df t1{__shfl_up_sync(0xffffffffu, s1.hi, d), __shfl_up_sync(0xffffffffu, s1.lo, d)};
+        df t2{__shfl_up_sync(0xffffffffu, s2.hi, d), __shfl_up_sync(0xffffffffu, s2.lo, d)};
+        if (lane < d) {
+            t1 = df{0.f, 0.f};
+            t2 = df{0.f, 0.f};
+        }
+        const float4 h = phi[j], l = phi_lo[j];
+        s1 = df_add(s1, df_add(df_mul(df{h.x, l.x}, t1), df_mul(df{h.y, l.y}, t2)));
+        s2 = df_add(s2, df_add(df_mul(df{h.z, l.z}, t1), df_mul(df{h.w, l.w}, t2)));
+    }
+    df e1{__shfl_up_sync(0xffffffffu, s1.hi, 1), __shfl_up_sync(0xffffffffu, s1.lo, 1)};
+    df e2{__shfl_up_sync(0xffffffffu, s2.hi, 1), __shfl_up_sync(0xffffffffu, s2.lo, 1)};
+    if (lane == 0) {
+        e1 = df{0.f, 0.f};
+        e2 = df{0.f, 0.f};
+    }
+    // fold the group's incoming state into this lane's: Phi^lane Z + E
+    const df zin1 = df_add(e1, df_add(df_mul(df{lp.x, lpl.x}, Z1), df_mul(df{lp.y, lpl.y}, Z2)));
+    const df zin2 = df_add(e2, df_add(df_mul(df{lp.z, lpl.z}, Z1), df_mul(df{lp.w, lpl.w}, Z2)));
+    // S4 (iii): the re-run from the true lane state
+    {
+        const df y0 = df_add(df{vh[0], vl[0]}, zin1);
+        const df y1 = df_rec1(df_add(df{vh[1], vl[1]}, zin2), q.a1, y0);
+        vh[0] = y0.hi;
+        vl[0] = y0.lo;
+        vh[1] = y1.hi;
+        vl[1] = y1.lo;
+    }
+#pragma unroll
+    for (int m = 2; m < N; ++m) {
+        const df y = df_rec(df{vh[m], vl[m]}, q.a1, df{vh[m - 1], vl[m - 1]}, q.a2,
+                            df{vh[m - 2], vl[m - 2]});
+        vh[m] = y.hi;
+        vl[m] = y.lo;
+    }
+    // the group's outgoing state, from lane 31's last two inputs and outputs
+    const df yl1{vh[N - 1], vl[N - 1]}, yl2{vh[N - 2], vl[N - 2]};
+    const df o1 = df_rec1(df_dot3(q.b1, xl1, q.b2, xl2, na1, yl1), q.a2, yl2);
+    const df o2 = df_rec1(df_mul(q.b2, xl1), q.a2, yl1);
+    Z1 = df{__shfl_sync(0xffffffffu, o1.hi, 31), __shfl_sync(0xffffffffu, o1.lo, 31)};
+    Z2 = df{__shfl_sync(0xffffffffu, o2.hi, 31), __shfl_sync(0xffffffffu, o2.lo, 31)};
+    // S8: final state at the channel's last sample
+    if (ZF) {
+        df yq, yqm1;
+        pick_pair<N>(vh, mq, yq.hi, yqm1.hi);
+        pick_pair<N>(vl, mq, yq.lo, yqm1.lo);
+        df f1;
+        if (mq >= 1) f1 = df_rec1(df_dot3(q.b1, xq, q.b2, xqm1, na1, yq), q.a2, yqm1);
+        else f1 = df_add(df_dot3(q.b1, xq, na1, yq, df{0.f, 0.f}, df{0.f, 0.f}), zin2);
+        const df f2 = df_rec1(df_mul(q.b2, xq), q.a2, yq);
+        if (zf_owner) {
+            zf_dst[0] = df_to_float(f1);
+            zf_dst[1] = df_to_float(f2);
         }
     }
 }

@@ -79,13 +79,35 @@ __device__ __forceinline__ float coef_sensitivity(double a1, double a2) {
     return (r * da1 + da2) / (sep * gap);
 }
 
+// Condition number of one normalised section, kappa = ||g|| ||b|| / ||h||:
+// g the impulse response of 1 / (1 + a1 z^-1 + a2 z^-2), h that of the whole
+// section, b = (b0, b1, b2).  Closed forms from the autocorrelation of the
+// all-pole part: c0 = ||g||^2 = (1 + a2) / ((1 - a2) ((1 + a2)^2 - a1^2)),
+// c1 = -a1 c0 / (1 + a2), c2 = -a1 c1 - a2 c0, and ||h||^2 = (b0^2 + b1^2 +
+// b2^2) c0 + 2 (b0 b1 + b1 b2) c1 + 2 b0 b2 c2.  Infinite for a pole on or
+// outside the unit circle or a vanishing response.  FP64, one lane.
+__device__ __forceinline__ double section_kappa(double b0, double b1, double b2, double a1,
+                                                double a2) {
+    const double d = (1.0 - a2) * ((1.0 + a2) * (1.0 + a2) - a1 * a1);
+    if (!(d > 0.0) || !(1.0 + a2 > 0.0)) return INFINITY;
+    const double c0 = (1.0 + a2) / d;
+    const double c1 = -a1 * c0 / (1.0 + a2);
+    const double c2 = -a1 * c1 - a2 * c0;
+    const double bb = b0 * b0 + b1 * b1 + b2 * b2;
+    const double hh = bb * c0 + 2.0 * (b0 * b1 + b1 * b2) * c1 + 2.0 * b0 * b2 * c2;
+    if (!(bb > 0.0)) return 0.0;  // no numerator: nothing to amplify
+    if (!(hh > 0.0)) return INFINITY;
+    return sqrt(c0 * bb / hh);
+}
+
 __device__ __forceinline__ bool finite_row(const double* r) {
     for (int i = 0; i < 6; ++i)
         if (!isfinite(r[i])) return false;
     return true;
 }
 
-constexpr int kPlanWarps = kMaxSections + 2;  // one per section + two horizon warps
+constexpr int kPlanWarps = kMaxSections + 3;  // one per section, two horizon warps, one
+                                              // for the precision estimate
 constexpr int kPlanThreads = kPlanWarps * 32;
 
 // complex FP32 helpers for the horizon bound
@@ -283,6 +305,148 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
     return !__any_sync(0xffffffffu, bad);
 }
 
+// Relative output error that FP32 rounding of the signal handed from section
+// k to section k + 1 causes, for a white input, at most over k (one warp):
+// the rounding adds white noise of relative size 2^-24 to y_k, whose power is
+// ||h_1..k||^2 per unit input power, and the sections after k pass it with
+// gain ||h_k+1..K||^2, against an output of power ||h_1..K||^2, so
+//   e = 2^-24 max_k ||h_1..k|| ||h_k+1..K|| / ||h_1..K||.
+// The norms come in closed form from the partial fractions of each partial
+// cascade (no truncated response, whatever the poles' distance from the unit
+// circle): with residues R_i at the poles p_i, sum_n |h[n]|^2 = h[0]^2 +
+// Re sum_{i,j} R_i conj(R_j) q_ij / (1 - q_ij), q_ij = p_i conj(p_j).  Lane i
+// < 2K takes pole i; its residue in the cascade of sections a..b is the
+// product over m in a..b of F_i(m) = B_m(p_i) / prod of (1 - p_l / p_i) over
+// the poles l != i of section m, so prefixes and suffixes are running
+// products.  Numerators enter scaled by 1 / max |b_j| (the scales cancel in
+// the ratio).  Returns the estimate, or -1 where it cannot be formed (a pole
+// at zero or coincident poles, a sum that cancels, overflow).
+__device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5], int K, int lane,
+                               cpx* s_pole) {
+    const int np = 2 * K;
+    if (K < 2) return 0x1p-24f;  // one section: nothing handed on
+    if (lane < np) {
+        const double a1 = rows[lane >> 1][3], a2 = rows[lane >> 1][4];
+        const double disc = a1 * a1 - 4.0 * a2;
+        cpx z;
+        if (disc < 0.0) {
+            const float im = 0.5f * sqrtf((float)(-disc));
+            z = cpx{(float)(-0.5 * a1), (lane & 1) ? -im : im};
+        } else {
+            const double sq = sqrt(disc);
+            z = cpx{(float)(0.5 * ((lane & 1) ? -a1 - sq : -a1 + sq)), 0.f};
+        }
+        s_pole[lane] = z;
+    }
+    __syncwarp();
+    bool bad = false;
+    const int sec = lane >> 1;
+    cpx W[2 * kMaxSections];   // q_ij / (1 - q_ij), j < 2K
+    cpx F[kMaxSections];       // F_i(m)
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxSections; ++j) W[j] = cpx{0.f, 0.f};
+#pragma unroll
+    for (int m = 0; m < kMaxSections; ++m) F[m] = cpx{1.f, 0.f};
+    if (lane < np) {
+        const cpx pi = s_pole[lane];
+        const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
+        if (!(r2 > 1e-24f)) bad = true;
+        const float ir2 = r2 > 1e-24f ? 1.f / r2 : 0.f;
+        const cpx inv{pi.re * ir2, -pi.im * ir2};
+        const cpx inv2 = cmul(inv, inv);
+#pragma unroll
+        for (int j = 0; j < 2 * kMaxSections; ++j) {
+            if (j < np) {
+                const cpx pj = s_pole[j];
+                const cpx q = cmul(pi, cpx{pj.re, -pj.im});
+                const cpx d{1.f - q.re, -q.im};
+                if (!(fmaf(d.re, d.re, d.im * d.im) > 1e-30f)) bad = true;
+                W[j] = cdiv(q, d);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < kMaxSections; ++m) {
+            if (m < K) {
+                const float ims = 1.f / num_scale(rowsf[m]);
+                const float b0 = rowsf[m][0] * ims, b1 = rowsf[m][1] * ims, b2 = rowsf[m][2] * ims;
+                cpx f{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int l = 2 * m + u;
+                    if (l != lane) {
+                        const cpx g = cmul(s_pole[l], inv);
+                        const cpx h{1.f - g.re, -g.im};
+                        if (fmaf(h.re, h.re, h.im * h.im) < 1e-8f) bad = true;
+                        f = cdiv(f, h);
+                    }
+                }
+                F[m] = f;
+            }
+        }
+    }
+    // energy of the cascade whose residue at this lane's pole is R (0 for
+    // poles outside it), with h[0] = h0; false if the sum cancels
+    auto energy = [&](cpx R, float h0, float& E) {
+        float e = 0.f, ea = 0.f;
+#pragma unroll
+        for (int j = 0; j < 2 * kMaxSections; ++j) {
+            if (j < np) {
+                const cpx Rj{__shfl_sync(0xffffffffu, R.re, j), __shfl_sync(0xffffffffu, R.im, j)};
+                const cpx t = cmul(cmul(R, cpx{Rj.re, -Rj.im}), W[j]);
+                e += t.re;
+                ea += cabs_(t);
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            e += __shfl_xor_sync(0xffffffffu, e, o);
+            ea += __shfl_xor_sync(0xffffffffu, ea, o);
+        }
+        E = fmaf(h0, h0, e);
+        return E > 0.f && E >= 1e-4f * ea && E < 1e30f;
+    };
+    float Epre[kMaxSections], Esuf[kMaxSections];
+    bool ok = true;
+    {
+        // prefixes 0..j
+        cpx P{1.f, 0.f};
+        float h0 = 1.f;
+#pragma unroll
+        for (int j = 0; j < kMaxSections; ++j) {
+            Epre[j] = 1.f;
+            if (j < K) {
+                P = cmul(P, F[j]);
+                h0 *= rowsf[j][0] / num_scale(rowsf[j]);
+                const cpx R = (lane < np && sec <= j) ? P : cpx{0.f, 0.f};
+                ok = energy(R, h0, Epre[j]) && ok;
+            }
+        }
+    }
+    {
+        // suffixes k..K-1
+        cpx P{1.f, 0.f};
+        float h0 = 1.f;
+#pragma unroll
+        for (int k = kMaxSections - 1; k >= 1; --k) {
+            Esuf[k] = 1.f;
+            if (k < K) {
+                P = cmul(P, F[k]);
+                h0 *= rowsf[k][0] / num_scale(rowsf[k]);
+                const cpx R = (lane < np && sec >= k) ? P : cpx{0.f, 0.f};
+                ok = energy(R, h0, Esuf[k]) && ok;
+            }
+        }
+        Esuf[0] = 1.f;
+    }
+    if (__any_sync(0xffffffffu, bad) || !ok) return -1.f;
+    float amp = 0.f;
+#pragma unroll
+    for (int k = 0; k + 1 < kMaxSections; ++k)
+        if (k + 1 < K) amp = fmaxf(amp, Epre[k] * Esuf[k + 1]);
+    amp = sqrtf(amp / Epre[K - 1]);
+    if (!(amp < 1e30f)) return -1.f;
+    return 0x1p-24f * fmaxf(amp, 1.f);
+}
+
 // The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp), and
 // the channel's segment length: the call's T, or longer when the horizon
 // needs it (a segment is at least 2 P and long enough for the initial
@@ -379,7 +543,10 @@ __device__ __forceinline__ void plan_table(const Params& p) {
 }
 
 // Block c < C: the coefficient tables and the memory horizon of channel c.
-__device__ __forceinline__ void plan_channel(const Params& p) {
+// Returns false when the channel's tables were kept from the previous plan on
+// this workspace (plan cache: same raw sos rows bit for bit, same K and
+// length, same call-level inputs), true when they were recomputed.
+__device__ __forceinline__ bool plan_channel(const Params& p) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int kmax = p.kmax;
 
@@ -396,12 +563,15 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     __shared__ float s_rowf[kMaxSections][5];  // the same rows rounded to FP32
     __shared__ double s_G[kMaxSections];
     __shared__ float s_Ginv[kMaxSections];      // 1 / G_k
-    __shared__ float s_dfscan[kMaxSections];    // 1: extended-precision section
+    __shared__ float s_dfscan[kMaxSections];    // the section's precision level (misc.w)
+    __shared__ float s_kappa[kMaxSections];     // section_kappa()
+    __shared__ float s_handoff;                 // handoff_error(), -1 if unknown
     __shared__ double s_b0inv[kMaxSections];    // 1 / b0 (normalised), 0 if b0 = 0
     __shared__ float s_h2;                      // ||h||_2 lower bound
     __shared__ int s_mode, s_horizon, s_err;
     __shared__ cpx s_pole[2 * kMaxSections];
     __shared__ cpx s_res[2 * kMaxSections];
+    __shared__ cpx s_pole2[2 * kMaxSections];  // the precision warp's copy
     // [0..4] Phi^(2^j); [5..9] Psi^(2^r); [10..19] Theta^(2^i)
     __shared__ dfm2 s_chain[kMaxSections][20];
 
@@ -417,7 +587,53 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     const int Kc = (K >= 0 && K <= kmax) ? K : 0;
     const bool active = k < Kc;
     if (tid == 0) s_err = 0;
+
+    // ---- plan cache: are this channel's tables those of these inputs? ----
+    unsigned char* kb = p.key + chan_key_stride(kmax) * (size_t)c;
+    ChanKeyHead* kh = reinterpret_cast<ChanKeyHead*>(kb);
+    unsigned long long* krow = reinterpret_cast<unsigned long long*>(kb + sizeof(ChanKeyHead));
+    __shared__ int s_same[kMaxSections + 1];
+    // (every value is loaded before any is compared: a short-circuit chain
+    // would make the loads wait for one another)
+    if (lane == 0 && k < kMaxSections) {
+        unsigned long long diff = 0;
+        if (k < Kc) {
+            unsigned long long st[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) st[i] = krow[k * 6 + i];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) diff |= (unsigned long long)__double_as_longlong(row[i]) ^ st[i];
+        }
+        s_same[k] = diff == 0;
+    }
+    if (tid == 0) {
+        const WsHeader* h = p.hdr;
+        const int32_t hv = h->key_valid, hN = h->key_N, hW = h->key_W, ha = h->key_algo,
+                      hf = h->key_flags, hk = h->key_kmax, hC = h->key_C;
+        const int64_t hs = h->key_seg, hc = h->key_cap;
+        const int32_t kv = kh->valid, kK = kh->K;
+        const int64_t kl = kh->len, len = p.lengths[c];
+        const bool same = !(p.flags_opt & SOS_FLAG_REPLAN) & (hv == 1) & (hN == p.N) &
+                          (hW == p.W) & (ha == p.algo) & (hf == p.flags_opt) & (hk == kmax) &
+                          (hC == p.C) & (hs == p.seg) & (hc == p.cap_tiles) & (kv == 1) &
+                          (kK == K) & (kl == len);
+        s_same[kMaxSections] = same;
+    }
     __syncthreads();
+    {
+        bool reuse = true;
+        for (int i = 0; i <= kMaxSections; ++i) reuse = reuse && s_same[i] != 0;
+        if (reuse) return false;
+    }
+    // recomputing: record the inputs the new tables are built from (read only
+    // by the next plan launch on this workspace)
+    if (lane == 0 && k < Kc)
+        for (int i = 0; i < 6; ++i) krow[k * 6 + i] = (unsigned long long)__double_as_longlong(row[i]);
+    if (tid == 0) {
+        kh->K = K;
+        kh->len = p.lengths[c];
+        kh->valid = 1;
+    }
     // lane 0 of each section warp normalises its row in FP64 (the FP64 unit is
     // narrow on this part: one lane per row, not the whole warp)
     if (lane == 0 && k < kMaxSections) {
@@ -486,7 +702,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
         const float h2 = carry_only ? 0.f : horizon_norm(s_rowf, Kc, lane);
         if (lane == 0) s_h2 = h2;
         asm volatile("bar.arrive 3, 64;" ::: "memory");
-        return;
+        return true;
     }
     if (warp == kMaxSections + 1) {
         // the second horizon warp: the memory horizon of channel c (against
@@ -525,10 +741,19 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
         }
         // release the section warps waiting for the decision (barrier 2:
         // the Kc section warps and this one)
-        if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
-        return;
+        if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 2)) : "memory");
+        return true;
     }
-    if (!active) return;
+    if (warp == kMaxSections + 2) {
+        // the precision warp: how much FP32 rounding between sections would
+        // cost at the output (released with barrier 2)
+        const bool skip = carry_only || (p.flags_opt & kFlagBackwardPlan) || Kc == 0;
+        const float e = skip ? 0.f : handoff_error(s_row, s_rowf, Kc, lane, s_pole2);
+        if (lane == 0) s_handoff = e;
+        if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 2)) : "memory");
+        return true;
+    }
+    if (!active) return true;
 
     // ---- Phi: double-float squaring chain (lane 0) ----
     const int N = p.N, W = p.W;
@@ -602,9 +827,12 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
     }
     if (lane == 0) {
         // extended precision (FP64 work on one lane: the FP64 pipe is narrow)
-        const float ext =
-            (m > kDfScanEntry || coef_sensitivity(a1, a2) > (float)kDfCoefSens) ? 1.f : 0.f;
+        const float sens = coef_sensitivity(a1, a2);
+        const float ext = (m > kDfScanEntry || sens > (float)kDfCoefSens)
+                              ? 2.f
+                              : (sens > (float)kAloCoefSens ? 1.f : 0.f);
         s_dfscan[k] = ext;
+        s_kappa[k] = (float)section_kappa(b0, b1, b2, a1, a2);
         // b1 / b0 and b2 / b0 when b0 is factored (1 / b0 from the rows phase)
         const double sb = mode ? s_b0inv[k] : 1.0;
         out32->ab = make_float4((float)a1, (float)a2, (float)(b1 * sb), (float)(b2 * sb));
@@ -612,17 +840,31 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
                                  0.0f, 0.0f);
         out32->misc = make_float4((float)b0, (float)s_G[k], s_Ginv[k], ext);
         out32->braw = make_float4((float)b0, (float)b1, (float)b2, 0.0f);
+        out32->blo = make_float4((float)(b0 - (double)(float)b0), (float)(b1 - (double)(float)b1),
+                                 (float)(b2 - (double)(float)b2), 0.0f);
     }
 
     // ---- Psi = A^(NL) and Theta = A^T, only for channels carried by the
     // look-back (its warp and tile steps) ----
-    asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 1)) : "memory");
+    asm volatile("bar.sync 2, %0;" ::"r"(32 * (Kc + 2)) : "memory");
     if (k == 0 && lane == 0) {
+        // the channel's precision class: the largest section level, or 3
+        // (double-float samples) for a channel within its memory horizon
+        // whose hand-off error estimate is too large (or unknown while some
+        // section is ill-conditioned), or when the call asks for it
         int16_t e = 0;
-        for (int j = 0; j < Kc; ++j) e |= s_dfscan[j] != 0.f ? 1 : 0;
+        float kap = 0.f;
+        for (int j = 0; j < Kc; ++j) {
+            e = (int16_t)max((int)e, (int)s_dfscan[j]);
+            kap = fmaxf(kap, s_kappa[j]);
+        }
+        const float h = s_handoff;
+        const bool whole = (p.flags_opt & SOS_FLAG_DOUBLE_FLOAT) || h > kHandOffErrMax ||
+                           (h < 0.f && e > 0) || !(kap * 0x1p-24f <= kHandOffErrMax);
+        if (whole && s_horizon >= 0 && !(p.flags_opt & kFlagBackwardPlan)) e = 3;
         p.chan[c].ext = e;
     }
-    if (s_horizon >= 0) return;
+    if (s_horizon >= 0) return true;
     if (lane == 0) {
         dfm2 P = dfm_mul(s_chain[k][4], s_chain[k][4]);  // Psi = Phi^32
         s_chain[k][5] = P;
@@ -667,6 +909,7 @@ __device__ __forceinline__ void plan_channel(const Params& p) {
             outdf->theta_pow[32][1] = make_float4(T32.c.hi, T32.c.lo, T32.d.hi, T32.d.lo);
         }
     }
+    return true;
 }
 
 // Dispatch (the whole CTA that finishes the plan last).  First the
@@ -827,11 +1070,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
     // it reads anything the plan writes)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     extern __shared__ unsigned long long s_key[];
-    __shared__ int s_last;
+    __shared__ int s_last, s_changed;
+    bool changed = false;
     if ((int)blockIdx.x == p.C) plan_table(p);
-    else plan_channel(p);
+    else changed = plan_channel(p);
     __syncthreads();
     if (threadIdx.x == 0) {
+        if (changed) atomicAdd(&p.hdr->plan_changed, 1u);
         __threadfence();  // this block's tables before its arrival
         const unsigned prev = atomicAdd(&p.hdr->plan_done, 1u);
         s_last = prev == (unsigned)p.C;  // C + 1 blocks
@@ -840,7 +1085,27 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Params p) {
     __syncthreads();
     if (!s_last) return;
     __threadfence();  // every block's tables before the order pass reads them
-    order_pass(p, s_key);
+    if (threadIdx.x == 0) s_changed = (int)__ldcg(&p.hdr->plan_changed);
+    __syncthreads();
+    // every channel kept its tables (which implies the same call-level
+    // inputs): the prefixes and the dispatch order are those of the previous
+    // plan as well
+    if (s_changed != 0) order_pass(p, s_key);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        WsHeader* h = p.hdr;
+        h->key_N = p.N;
+        h->key_W = p.W;
+        h->key_algo = p.algo;
+        h->key_flags = p.flags_opt;
+        h->key_kmax = p.kmax;
+        h->key_C = p.C;
+        h->key_seg = p.seg;
+        h->key_cap = p.cap_tiles;
+        h->key_valid = 1;
+        h->last_recomputed = s_changed;
+        h->plan_changed = 0;
+    }
 }
 
 cudaError_t launch_plan(const Params& p, cudaStream_t stream) {

@@ -42,9 +42,28 @@ struct WsHeader {
     int64_t total_pipe;     // segments of the section pipeline (channels within their horizon)
     unsigned long long seg_next;  // warp-segment kernel: segments handed out past the first round
     uint32_t seg_done;      // warp-segment kernel: warps of the running launch that have finished
-    uint32_t pad1;
+    uint32_t spin_limit;    // bound on each device-side wait (0 = the compiled default)
+    // plan cache: the call-level inputs of the latest complete plan on this
+    // workspace (key_valid = 1), so that the next plan can tell whether a
+    // channel's tables are still those of its inputs
+    int32_t key_valid, key_N, key_W, key_algo, key_flags, key_kmax, key_C;
+    uint32_t plan_changed;  // channels recomputed by the running plan launch
+    int64_t key_seg, key_cap;
+    int32_t last_recomputed;  // channels the latest plan recomputed
+    uint32_t pad2[3];
 };
-static_assert(sizeof(WsHeader) == 64, "header size");
+static_assert(sizeof(WsHeader) == 128, "header size");
+
+// Per-channel record of the plan cache: the raw sos rows (bit patterns), K
+// and length from which the channel's tables were last built.
+struct ChanKeyHead {
+    int64_t len;
+    int32_t K;
+    int32_t valid;
+};
+__host__ __device__ inline size_t chan_key_stride(int32_t kmax) {
+    return sizeof(ChanKeyHead) + sizeof(double) * 6 * (size_t)kmax;
+}
 
 struct ChanInfo {
     int64_t off;      // first sample of the channel in the packed arrays
@@ -57,7 +76,8 @@ struct ChanInfo {
     int32_t horizon;  // >= 0: memory horizon P (segments start P samples early, no
                       // carry); -1: the state is carried by the look-back
     int16_t single;   // 1: the whole channel is one segment (backward plans)
-    int16_t ext;      // 1: some section runs in extended precision (Coef32::misc.w)
+    int16_t ext;      // precision class: 0 FP32; 1, 2: the largest section level
+                      // (Coef32::misc.w); 3: double-float samples throughout
     int64_t seg;      // segment length of a channel with a horizon (a multiple of 32 N,
                       // at least 2 P)
 };
@@ -110,17 +130,37 @@ struct __align__(16) Coef32 {
     float4 phi_lo[5];
     float4 lane_lo[32];
     float4 alo;
+    // read by channels run with double-float samples: the low parts of b0,
+    // b1, b2 normalised by a0 (never factored; braw holds the high parts)
+    float4 blo;
 };
 
-// A section runs in extended precision (misc.w) when the largest entry of
-// its powers Phi^(2^j), Phi^l exceeds kDfScanEntry (poles close to z = +-1
-// near the unit circle: the entries grow to about min(l N, 1 / sin(theta))
-// and the FP32 products of the lane scan cancel), or when rounding a1, a2 to
-// FP32 moves its poles by more than kDfCoefSens of their distance to the
-// circle.  Its lane scan and fold then run in double-float and its in-lane
-// recursions add the coefficients' low parts (two FMAs per sample and pass).
+// Extended precision per section (Coef32::misc.w).  Level 2 when the
+// largest entry of its powers Phi^(2^j), Phi^l exceeds kDfScanEntry (poles
+// close to z = +-1 near the unit circle: the entries grow to about
+// min(l N, 1 / sin(theta)) and the FP32 products of the lane scan cancel), or
+// when rounding a1, a2 to FP32 moves its poles by more than kDfCoefSens of
+// their distance to the circle: the lane scan and fold run in double-float
+// and the in-lane recursions add the coefficients' low parts.  Level 1 when
+// that displacement exceeds kAloCoefSens only: the low parts alone (two FMAs
+// per sample and pass).  The output's relative error from rounding a1, a2
+// is about that displacement, so level 1 keeps it below 2^-18.
 constexpr float kDfScanEntry = 8.f;
 constexpr double kDfCoefSens = 1e-4;
+constexpr double kAloCoefSens = 0x1p-18;
+
+// A channel is run with double-float samples throughout (ChanInfo::ext = 3)
+// when the relative error that FP32 rounding of the signals handed from one
+// section to the next would cause at the output, estimated by the plan for a
+// white input, exceeds kHandOffErrMax (or when the estimate cannot be formed
+// and some section is ill-conditioned), or when a section's own FP32
+// rounding is amplified beyond the same bound: rounding its FIR output or its
+// recursion adds white noise of relative size 2^-24, which its all-pole part
+// passes with gain ||g|| (g the all-pole impulse response) against a signal
+// passed with the whole section's gain ||h|| per unit ||b||, so the section's
+// condition number kappa = ||g|| ||b|| / ||h|| (zeros close to the poles make
+// it large) must stay below kHandOffErrMax * 2^24.
+constexpr float kHandOffErrMax = 0x1p-17f;
 
 // Per (channel, section) double-float powers of the tile transition
 // Theta = A^T (T = tile length) for the cross-tile composition, each as
@@ -142,7 +182,7 @@ struct __align__(16) CoefDF {
 constexpr int kWords = 6;  // inc z1.hi, z1.lo, z2.hi, z2.lo, agg z1, z2
 
 struct WsLayout {
-    size_t hdr, chan, tb, tbp, order, rp, c32, cdf, slots, total;
+    size_t hdr, chan, tb, tbp, order, rp, c32, cdf, key, slots, total;
     int64_t cap_tiles;
 };
 
@@ -161,6 +201,7 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.rp = o;    o = align_up(o + sizeof(int64_t) * (2 * (size_t)(cap_tiles > 0 ? cap_tiles : 0) + 2), 256);
     L.c32 = o;   o = align_up(o + sizeof(Coef32) * (size_t)C * kmax, 256);
     L.cdf = o;   o = align_up(o + sizeof(CoefDF) * (size_t)C * kmax, 256);
+    L.key = o;   o = align_up(o + chan_key_stride(kmax) * (size_t)C, 256);
     const size_t nt = (size_t)(cap_tiles > 0 ? cap_tiles : 1);
     L.slots = o; o = align_up(o + sizeof(unsigned long long) * kWords * nt * kmax, 256);
     L.total = o;
@@ -185,6 +226,7 @@ struct Params {
     int64_t* rp;         // tiles dispatched before round r [nrounds + 1]
     Coef32* c32;
     CoefDF* cdf;
+    unsigned char* key;  // plan cache: per channel a ChanKeyHead and kmax raw sos rows
     unsigned long long* words;  // look-back words [kmax][kWords][cap_tiles]
     int64_t cap_tiles;
     int32_t C;
@@ -255,6 +297,13 @@ __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
 
 __device__ __forceinline__ void set_status(WsHeader* h, int32_t s) {
     atomicCAS(&h->status, 0, s);
+}
+
+// The bound on a device-side wait: the workspace's spin_limit when set (a
+// caller may shorten it to test the time-out path), else the compiled default.
+__device__ __forceinline__ uint32_t wait_limit(const WsHeader* h, uint32_t dflt) {
+    const uint32_t v = *reinterpret_cast<const volatile uint32_t*>(&h->spin_limit);
+    return v ? v : dflt;
 }
 
 }  // namespace sosf

@@ -110,4 +110,50 @@ __device__ __forceinline__ void dfm_affine_fast(const dfm2& M, df u1, df u2, df 
 
 __device__ __forceinline__ float df_to_float(df a) { return a.hi + a.lo; }
 
+// ---------------------------------------------------------------------------
+// Double-float signal arithmetic for the sample recursions of channels run in
+// extended precision.  A sample is (hi, lo); products use the FMA-based
+// TwoProduct, sums of the leading parts Knuth's TwoSum, and every low-order
+// term (the products' errors, the sums' errors, the cross terms hi*lo) is
+// collected in one FP32 accumulator, then renormalised once (Fast2Sum).  The
+// error of one such step is about 2^-44 of its operands.
+
+// a0*x0 + a1*x1 + a2*x2 (coefficients and samples double-float)
+__device__ __forceinline__ df df_dot3(df a0, df x0, df a1, df x1, df a2, df x2) {
+    const float p0 = a0.hi * x0.hi, p1 = a1.hi * x1.hi, p2 = a2.hi * x2.hi;
+    float c = fmaf(a0.hi, x0.hi, -p0);
+    c += fmaf(a1.hi, x1.hi, -p1);
+    c += fmaf(a2.hi, x2.hi, -p2);
+    const df s1 = df_two_sum(p0, p1);
+    const df s2 = df_two_sum(s1.hi, p2);
+    c += s1.lo + s2.lo;
+    c = fmaf(a0.hi, x0.lo, fmaf(a0.lo, x0.hi, c));
+    c = fmaf(a1.hi, x1.lo, fmaf(a1.lo, x1.hi, c));
+    c = fmaf(a2.hi, x2.lo, fmaf(a2.lo, x2.hi, c));
+    return df_fast_two_sum(s2.hi, c);
+}
+
+// u - a1*y1 - a2*y2: one step of the all-pole recursion
+__device__ __forceinline__ df df_rec(df u, df a1, df y1, df a2, df y2) {
+    const float p1 = a1.hi * y1.hi, p2 = a2.hi * y2.hi;
+    float c = u.lo - fmaf(a1.hi, y1.hi, -p1);
+    c -= fmaf(a2.hi, y2.hi, -p2);
+    const df s1 = df_two_sum(u.hi, -p1);
+    const df s2 = df_two_sum(s1.hi, -p2);
+    c += s1.lo + s2.lo;
+    c = fmaf(-a1.hi, y1.lo, fmaf(-a1.lo, y1.hi, c));
+    c = fmaf(-a2.hi, y2.lo, fmaf(-a2.lo, y2.hi, c));
+    return df_fast_two_sum(s2.hi, c);
+}
+
+// u - a1*y1 (the second sample of a run, one history term)
+__device__ __forceinline__ df df_rec1(df u, df a1, df y1) {
+    const float p1 = a1.hi * y1.hi;
+    float c = u.lo - fmaf(a1.hi, y1.hi, -p1);
+    const df s1 = df_two_sum(u.hi, -p1);
+    c += s1.lo;
+    c = fmaf(-a1.hi, y1.lo, fmaf(-a1.lo, y1.hi, c));
+    return df_fast_two_sum(s1.hi, c);
+}
+
 }  // namespace sosf

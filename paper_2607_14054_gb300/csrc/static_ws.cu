@@ -41,6 +41,11 @@ extern "C" sos_status sos_filter_static(const float* x, const double* sos, const
     const size_t need = sos_workspace_size(n_channels, kmax, lengths_host, tuning);
     if (need == 0) return SOS_ERR_ARG;
     if (need > kStaticScratchBytes) return SOS_ERR_WORKSPACE;  // beyond the fixed maximum
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return SOS_ERR_CUDA;
+    // reading the device status waits for the stream, which a capture forbids
+    if (cap != cudaStreamCaptureStatusNone && device_status) return SOS_ERR_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SOS_ERR_CUDA;
     void* ws = nullptr;
@@ -49,10 +54,16 @@ extern "C" sos_status sos_filter_static(const float* x, const double* sos, const
         if (!g_addr[dev]) {
             // first call on this device: find the array's device address and
             // zero it once (the look-back epoch and the tile counter must start
-            // at zero; later calls keep them consistent themselves)
+            // at zero; later calls keep them consistent themselves).  The
+            // zeroing is ordered on the caller's stream and waited for here, so
+            // that it has finished before this or any later call, on any
+            // stream, touches the array.  A stream being captured cannot be
+            // waited for: the first call must come before any capture.
+            if (cap != cudaStreamCaptureStatusNone) return SOS_ERR_ARG;
             void* a = nullptr;
             if (cudaGetSymbolAddress(&a, g_static_scratch) != cudaSuccess || !a) return SOS_ERR_CUDA;
-            if (cudaMemset(a, 0, kStaticScratchBytes) != cudaSuccess) return SOS_ERR_CUDA;
+            if (cudaMemsetAsync(a, 0, kStaticScratchBytes, st) != cudaSuccess) return SOS_ERR_CUDA;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return SOS_ERR_CUDA;
             g_addr[dev] = a;
         }
         ws = g_addr[dev];

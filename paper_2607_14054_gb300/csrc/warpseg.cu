@@ -62,15 +62,33 @@ struct WsCursor {
     int a, b;          // the segment's own outputs, relative to the group start
 };
 
+// Precision class of a channel (ChanInfo::ext), which selects the
+// instantiation of the segment code that runs it.
+enum WsPrec {
+    kPrecF32 = 0,   // every section in FP32
+    kPrecSect = 1,  // sections flagged in Coef32::misc.w: 1 = coefficient low
+                    // parts in the in-lane recursions, 2 = also the lane scan and
+                    // fold in double-float
+    kPrecDF = 2     // the whole cascade with double-float samples
+};
+
+// The section coefficients of a channel run with double-float samples.
+__device__ __forceinline__ SecDF load_secdf(const Coef32* cf) {
+    const float4 ab = cf->ab, alo = cf->alo, br = cf->braw, bl = cf->blo;
+    return SecDF{df{ab.x, alo.x}, df{ab.y, alo.y}, df{br.x, bl.x}, df{br.y, bl.y},
+                 df{br.z, bl.z}};
+}
+
 // One group of a segment through all K sections: prefetch the next group,
 // filter this one in registers, store the segment's own outputs.  ZF: the
 // group holding the channel's last sample, whose final state (zf) is taken at
 // element mq of lane `owner`'s chunk; instantiated apart so that the hot
-// loop holds no zf code.  DFS: some section of the channel runs its lane scan
-// in double-float (Coef32::misc.w); instantiated apart for the same reason.
-template <int N, bool FACT, bool CR, bool ZF, bool DFS>
+// loop holds no zf code.  PREC: the channel's precision class (WsPrec);
+// instantiated apart for the same reason.  zs: the sections' DF2T states
+// (z1, z2 as float pairs hi, lo; the lo parts are used by kPrecDF only).
+template <int N, bool FACT, bool CR, bool ZF, int PREC>
 __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, float* slots,
-                                         float2* zs, int lane, int& cur, WsCursor& q, bool last,
+                                         float4* zs, int lane, int& cur, WsCursor& q, bool last,
                                          bool& pending, const float* nsrc, int64_t nrem,
                                          int owner, int mq) {
     using SL = SlotLayout<N>;
@@ -94,6 +112,27 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
     float* row = slot + lane * SL::kRow;
     float v[N];
     row_to_chunk<N>(v, row);
+    if (PREC == kPrecDF) {
+        // the whole cascade with double-float samples (the input is FP32:
+        // its low parts start at zero); the output is rounded once
+        float vl[N];
+#pragma unroll
+        for (int m = 0; m < N; ++m) vl[m] = 0.f;
+#pragma unroll 1
+        for (int k = 0; k < K; ++k) {
+            const Coef32* cf = cf0 + k;
+            const SecDF sd = load_secdf(cf);
+            const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane];
+            float* zf_dst = ZF ? p.zf + ((int64_t)sg.c * p.kmax + k) * 2 : nullptr;
+            const float4 zz = zs[k];
+            df z1{zz.x, zz.y}, z2{zz.z, zz.w};
+            pipe_section_dfx<N, ZF>(v, vl, sd, cf->phi_pow, cf->phi_lo, lp, lpl, z1, z2,
+                                    lane == owner, mq, zf_dst);
+            if (lane == 0) zs[k] = make_float4(z1.hi, z1.lo, z2.hi, z2.lo);
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) v[m] = v[m] + vl[m];
+    } else {
     // one copy of the section code (a rolled loop keeps the kernel's
     // instruction footprint inside the instruction cache); plain (L1-cached)
     // loads at the point of use: read-only loads would be hoisted out of the
@@ -105,23 +144,33 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
         const float b0 = FACT ? 1.f : cf->misc.x;
         const float G = (ZF && FACT) ? cf->misc.y : 1.f;
         float* zf_dst = ZF ? p.zf + ((int64_t)sg.c * p.kmax + k) * 2 : nullptr;
-        float2 z = zs[k];
+        const float4 zz = zs[k];
+        float2 z = make_float2(zz.x, zz.z);
+        const float lvl = PREC == kPrecSect ? cf->misc.w : 0.f;
         if (CR) {
             pipe_section_cr<N, FACT, ZF>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, lane == owner, mq,
                                          row, zf_dst, G);
-        } else if (DFS && cf->misc.w != 0.f) {
+        } else if (PREC == kPrecSect && lvl > 1.5f) {
             const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane], alo = cf->alo;
             pipe_section<N, FACT, ZF, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
                                                    lane == owner, mq, row, zf_dst, G, -1, 0.f,
                                                    0.f, cf->phi_lo, lpl,
                                                    make_float2(alo.x, alo.y));
+        } else if (PREC == kPrecSect && lvl > 0.5f) {
+            const float4 lp = cf->lane_pow[lane], alo = cf->alo;
+            pipe_section<N, FACT, ZF, false, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
+                                                          lane == owner, mq, row, zf_dst, G, -1,
+                                                          0.f, 0.f, nullptr,
+                                                          make_float4(0.f, 0.f, 0.f, 0.f),
+                                                          make_float2(alo.x, alo.y));
         } else {
             const float4 lp = cf->lane_pow[lane];
             pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
                                       row, zf_dst, G);
         }
         // every lane holds the outgoing state; the writes agree
-        if (lane == 0) zs[k] = z;
+        if (lane == 0) zs[k] = make_float4(z.x, 0.f, z.y, 0.f);
+    }
     }
     if (FACT) {
         const float Gk = cf0[K - 1].misc.y;
@@ -159,9 +208,9 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
 // slot `cur` holds the segment's first group if `pending`; on exit `cur` is
 // the slot of the next segment's first group, and `pending` says whether it
 // was issued (nsrc: that group's source, nullptr if none).
-template <int N, bool FACT, bool CR, bool DFS>
+template <int N, bool FACT, bool CR, int PREC>
 __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, float* slots,
-                                           float2* zs, int lane, int& cur, bool& pending,
+                                           float4* zs, int lane, int& cur, bool& pending,
                                            const float* nsrc, int64_t nrem) {
     using WC = WsCfg<N>;
     const int K = sg.K;
@@ -171,11 +220,11 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
     // zero state after a warm-up
     __syncwarp();
     if (lane < K) {
-        float2 z = make_float2(0.f, 0.f);
+        float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
         if (sg.si == 0 && p.zi) {
             const float gi = FACT ? __ldg(&cf0[lane].misc.z) : 1.f;
             z.x = __ldg(p.zi + ((int64_t)sg.c * p.kmax + lane) * 2 + 0) * gi;
-            z.y = __ldg(p.zi + ((int64_t)sg.c * p.kmax + lane) * 2 + 1) * gi;
+            z.z = __ldg(p.zi + ((int64_t)sg.c * p.kmax + lane) * 2 + 1) * gi;
         }
         zs[lane] = z;
     }
@@ -194,12 +243,12 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
     const bool zf_last = p.zf && sg.out_hi == sg.len;
     const int ghot = zf_last ? ng - 1 : ng;
     for (int g = 0; g < ghot; ++g)
-        ws_group<N, FACT, CR, false, DFS>(p, sg, slots, zs, lane, cur, q, g + 1 == ng, pending, nsrc,
-                                     nrem, 0, 0);
+        ws_group<N, FACT, CR, false, PREC>(p, sg, slots, zs, lane, cur, q, g + 1 == ng, pending,
+                                           nsrc, nrem, 0, 0);
     if (zf_last) {
         const int rel = (int)(sg.len - 1 - sg.cstart);
-        ws_group<N, FACT, CR, true, DFS>(p, sg, slots, zs, lane, cur, q, true, pending, nsrc, nrem,
-                                    (rel % WC::kGroup) / N, rel % N);
+        ws_group<N, FACT, CR, true, PREC>(p, sg, slots, zs, lane, cur, q, true, pending, nsrc,
+                                          nrem, (rel % WC::kGroup) / N, rel % N);
     }
 }
 
@@ -215,7 +264,7 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
     // its writes) before the first read of the plan's tables
     asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ float4 s_ws4[];
-    __shared__ float2 s_z[kWsWarps][kMaxSections];
+    __shared__ float4 s_z[kWsWarps][kMaxSections];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float* slots = reinterpret_cast<float*>(s_ws4) + (size_t)w * 2 * WC::kSlot;
     const int64_t total = p.hdr->total_pipe;  // segments of the latest plan
@@ -247,34 +296,39 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
             for (int64_t i = sg.out_lo + lane; i < sg.out_hi; i += 32)
                 p.y[sg.off + i] = __ldg(p.x + sg.off + i);
         } else {
-            const bool fact = p.chan[sg.c].mode != 0;
+            const ChanInfo& ci = p.chan[sg.c];
+            const bool fact = ci.mode != 0;
+            // the channel's precision class (sos_plan_extended): 3 = the whole
+            // cascade in double-float, 1..2 = some sections in extended
+            // precision, 0 = FP32
+            const int ext = ci.ext;
             // cyclic reduction when the call asks for it and every section of
-            // the channel is well conditioned for it, PH otherwise
-            bool cr = CRK;
+            // the channel is well conditioned for it (FP32 channels only), PH
+            // otherwise
+            bool cr = CRK && ext == 0;
             for (int k = 0; k < sg.K && cr; ++k)
                 cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
-            // PH sections whose lane scan runs in double-float
-            bool dfs = false;
-            for (int k = 0; k < sg.K && !dfs; ++k)
-                dfs = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].misc.w) != 0.f;
-            if (CRK && fact && cr)
-                ws_segment<N, true, CRK, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
-                                                nrem);
-            else if (CRK && cr)
-                ws_segment<N, false, CRK, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
-                                                 nrem);
-            else if (fact && dfs)
-                ws_segment<N, true, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
-                                                 nrem);
-            else if (fact)
-                ws_segment<N, true, false, false>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
-                                                  nrem);
-            else if (dfs)
-                ws_segment<N, false, false, true>(p, sg, slots, s_z[w], lane, cur, pending, nsrc,
-                                                  nrem);
-            else
-                ws_segment<N, false, false, false>(p, sg, slots, s_z[w], lane, cur, pending,
+            if (ext >= 3)
+                ws_segment<N, false, false, kPrecDF>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                     nsrc, nrem);
+            else if (CRK && fact && cr)
+                ws_segment<N, true, CRK, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
                                                    nsrc, nrem);
+            else if (CRK && cr)
+                ws_segment<N, false, CRK, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                    nsrc, nrem);
+            else if (fact && ext)
+                ws_segment<N, true, false, kPrecSect>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                      nsrc, nrem);
+            else if (fact)
+                ws_segment<N, true, false, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                     nsrc, nrem);
+            else if (ext)
+                ws_segment<N, false, false, kPrecSect>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                       nsrc, nrem);
+            else
+                ws_segment<N, false, false, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
+                                                      nsrc, nrem);
         }
         d = dn;
         if (d < total) sg = seg_geom<WC::kGroup>(p, d);
