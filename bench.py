@@ -3,16 +3,19 @@
 
 One step = one full call of the C ABI's sos_filter on the 16th-order (K = 8)
 Butterworth band-pass workload, 2^24 FP32 samples i.i.d. N(0, 1), one
-channel, zero initial state, inputs resident in HBM: sos_prepare (plan and
-dispatch order, one kernel) then sos_apply (the kernel for channels within
-their memory horizon -- warp segments or the section pipeline -- launched
-early behind the plan, then the look-back kernel, which finds no carried
-channel here, launched early behind that), replayed as one CUDA graph.  The
-tuning (N, W, solver, kernel) is chosen by the library's autotuner before the
-timed region.
-Prints one JSON line (rank 0), with the batched (4096 channels),
-differentiation (forward + backward, 256 x 2^16) and precision-stress
-(64 x 2^26, poles at radius 0.999..0.9999) workloads as extra fields.
+channel, zero initial state, inputs resident in HBM: sos_prepare (the plan
+kernel; the coefficients are unchanged from the previous step, so its plan
+cache keeps the tables after comparing them on the device) then sos_apply
+(the kernel for channels within their memory horizon -- warp segments or the
+section pipeline -- launched early behind the plan, then the look-back
+kernel, which finds no carried channel here, launched early behind that),
+replayed as one CUDA graph.  The same step with the plan recomputed every
+time is reported beside it.  The tuning (N, W, solver, kernel) is chosen by
+the library's autotuner before the timed region.
+Prints one JSON line (rank 0), with the low-pass (K = 1, 8192 samples:
+latency), batched (4096 channels), differentiation (forward + backward,
+256 x 2^16) and precision-stress (64 x 2^26, poles at radius 0.999..0.9999)
+workloads as extra fields, and the oracle parity of every one of them.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
 
@@ -155,49 +158,66 @@ def barrier(world: int):
         dist.barrier()
 
 
-def oracle_baseline(wl, target_seconds: float = 10.0, checks=()):
+class ParityJob:
+    """One workload's outputs to check against the oracle in the cpu_baseline
+    leg: every channel in full (relative L2 per channel, run in chunks of
+    channels so that host memory stays bounded) and, with `windows`, also
+    that many equal windows of each channel, each against the oracle's output
+    over the same span (computed from the channel's start)."""
+
+    def __init__(self, name, x, sos, K, lengths, zi, y, tol, windows=0, chunk=256,
+                 channels=None):
+        self.name, self.x, self.sos, self.K = name, x, sos, K
+        self.lengths, self.zi, self.y, self.tol = lengths, zi, y, tol
+        self.windows, self.chunk = windows, chunk
+        self.channels = channels  # None: all; else the channel indices checked
+
+    def run(self):
+        import numpy as np
+        import oracle
+        L = np.asarray(self.lengths, dtype=np.int64)
+        off = np.concatenate([[0], np.cumsum(L)])
+        sos = self.sos.cpu().numpy()
+        K = np.asarray(self.K.cpu() if hasattr(self.K, "cpu") else self.K)
+        zi = self.zi.cpu().double().numpy() if self.zi is not None else None
+        chans = np.arange(len(L)) if self.channels is None else np.asarray(self.channels)
+        errs, wins = [], []
+        for i0 in range(0, len(chans), self.chunk):
+            cs = chans[i0:i0 + self.chunk]
+            xs = np.concatenate([self.x[int(off[c]):int(off[c + 1])].cpu().double().numpy()
+                                 for c in cs])
+            ys = np.concatenate([self.y[int(off[c]):int(off[c + 1])].cpu().double().numpy()
+                                 for c in cs])
+            ref, _ = oracle.sosfilt(xs, sos[cs], K=K[cs], lengths=L[cs],
+                                    zi=zi[cs] if zi is not None else None)
+            o = np.concatenate([[0], np.cumsum(L[cs])])
+            for j in range(len(cs)):
+                r, g = ref[o[j]:o[j + 1]], ys[o[j]:o[j + 1]]
+                nr = np.linalg.norm(r)
+                errs.append(float(np.linalg.norm(g - r) / nr) if nr > 0 else 0.0)
+                if self.windows:
+                    w = len(r) // self.windows
+                    wins.append(max(float(np.linalg.norm(g[k * w:(k + 1) * w] - r[k * w:(k + 1) * w])
+                                          / np.linalg.norm(r[k * w:(k + 1) * w]))
+                                    for k in range(self.windows)))
+        errs = np.array(errs)
+        out = {"rel_l2": float(errs.max()), "rel_l2_median": float(np.median(errs)),
+               "tolerance": self.tol, "channels": int(len(chans)),
+               "samples": int(L[chans].sum()), "within_tolerance": int((errs <= self.tol).sum())}
+        if self.windows:
+            wins = np.array(wins)
+            out.update({"windows_per_channel": self.windows, "worst_window_rel_l2": float(wins.max()),
+                        "within_tolerance_every_window": int(((errs <= self.tol) &
+                                                              (wins <= self.tol)).sum())})
+        return out
+
+
+def oracle_baseline(wl, target_seconds: float = 10.0, jobs=()):
     """Times the FP64 oracle (as it stands) on the host cores: whole-signal
-    passes of the workload, repeated until ~target_seconds of CPU work.  Also
-    runs it on each check (name, x prefix, sos rows, zi rows or None, GPU
-    output prefix, tolerance[, factor]): the relative L2 error of the GPU path
-    against the oracle on causal prefixes of the benchmarked workloads.  With a
-    factor, the same filter run sample by sample in FP32 (scipy's sosfilt on
-    float32 data: what FP32 arithmetic itself gives on that channel) is
-    measured beside it, and the channel also counts as within
-    max(tolerance, factor x that error)."""
-    import numpy as np
+    passes of the workload, repeated until ~target_seconds of CPU work.  Then
+    runs the parity jobs: the GPU path's outputs on the benchmarked workloads
+    against the oracle, per channel."""
     import oracle
-    parity = {}
-    for chk in checks:
-        name, xs, sos_c, zi_c, yg, tol = chk[:6]
-        factor = chk[6] if len(chk) > 6 else None
-        zi_o = None if zi_c is None else zi_c.double().numpy().reshape(1, -1, 2)
-        ref, _ = oracle.sosfilt(xs.double().numpy(), sos_c.numpy(), zi=zi_o)
-        nref = np.linalg.norm(ref)
-        err = float(np.linalg.norm(yg.double().numpy() - ref) / nref)
-        prev = parity.get(name)
-        if prev is None:
-            prev = parity[name] = {"rel_l2": 0.0, "tolerance": tol, "channels": 0,
-                                   "samples": 0, "within_tolerance": 0}
-            if factor is not None:
-                prev.update({"fp32_sequential_rel_l2": 0.0, "fp32_factor": factor,
-                             "within_fp32_bound": 0, "worst_error_over_bound": 0.0})
-        prev["rel_l2"] = max(prev["rel_l2"], err)
-        prev["channels"] += 1
-        prev["samples"] += int(xs.numel())
-        prev["within_tolerance"] += int(err <= tol)
-        if factor is not None:
-            import scipy.signal
-            zi32 = None if zi_c is None else zi_c.numpy().astype(np.float32)
-            x32 = xs.numpy().astype(np.float32)
-            s32 = sos_c.numpy().astype(np.float32)
-            y32 = (scipy.signal.sosfilt(s32, x32) if zi32 is None
-                   else scipy.signal.sosfilt(s32, x32, zi=zi32)[0])
-            e32 = float(np.linalg.norm(y32.astype(np.float64) - ref) / nref)
-            prev["fp32_sequential_rel_l2"] = max(prev["fp32_sequential_rel_l2"], e32)
-            bound = max(tol, factor * e32)
-            prev["within_fp32_bound"] += int(err <= bound)
-            prev["worst_error_over_bound"] = max(prev["worst_error_over_bound"], err / bound)
     x = wl.x.detach().cpu().double().numpy()
     sos = wl.sos.cpu().numpy()
     K = wl.K.cpu().numpy()
@@ -212,11 +232,15 @@ def oracle_baseline(wl, target_seconds: float = 10.0, checks=()):
             break
     samples = x.size * reps
     threads = min(oracle.num_threads(), wl.n_channels)
+    parity = {}
+    t1 = time.perf_counter()
+    for job in jobs:
+        parity[job.name] = job.run()
     return {"value": samples / el / 1e9, "unit": "Gsamples/s", "cores": int(threads),
             "kind": "oracle",
             "sample": f"{reps} full passes of the {x.size}-sample workload ({el:.1f} s); "
                       f"FP64 sample-by-sample cascade, one thread per channel",
-            "seconds": el, "parity": parity}
+            "seconds": el, "parity": parity, "parity_seconds": time.perf_counter() - t1}
 
 
 def run_reference(args):
@@ -253,6 +277,32 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def copy_rates(x, stream, reps: int = 10):
+    """The box's own pinned host <-> device copy rates (GB/s) for buffers the
+    size of the step's input and output, each direction timed alone with CUDA
+    events: the ceiling of any end-to-end pass that moves them once."""
+    import torch
+    xh = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
+    yh = torch.empty(x.numel(), dtype=torch.float32, pin_memory=True)
+    xd = torch.empty_like(x)
+    nbytes = 4 * x.numel()
+    out = {}
+    for name, fn in (("h2d", lambda: xd.copy_(xh, non_blocking=True)),
+                     ("d2h", lambda: yh.copy_(xd, non_blocking=True))):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    return out
 
 
 def end_to_end(P, x, sos, stream, samples, world, args, tuning):
@@ -322,9 +372,67 @@ def profiled_traffic(kernel: str, samples: int):
     return prof["dram_bytes_per_launch"] * samples / prof["samples"]
 
 
+def graph_of(fn):
+    """fn() captured as one CUDA graph (after a warm-up call on the capture
+    stream)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g
+
+
+def replay_ms(g, steps: int, flush=None):
+    """Mean milliseconds per replay of g, CUDA events on the current stream
+    around each replay (flush written before each one, outside the events)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(steps)]
+    for i in range(steps):
+        if flush is not None:
+            flush.zero_()
+        evs[i][0].record(stream)
+        g.replay()
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    return sum(e[0].elapsed_time(e[1]) for e in evs) / steps
+
+
+def lowpass_leg(P, dev, steps: int = 50):
+    """2nd-order Butterworth low-pass on 8,192 samples (K = 1): the latency
+    of one whole call (prepare + apply, one graph replay; inputs resident,
+    small enough to stay in L2 between calls, as a real-time caller's
+    would)."""
+    import torch
+    from synth import workloads
+    wl = workloads.plain_lowpass(device=dev)
+    plan = P.SosFilter(wl.lengths, 1, device=dev)
+    y = torch.empty_like(wl.x)
+    zf = torch.empty(1, 1, 2, device=dev)
+
+    def call():
+        plan(wl.x, wl.sos, wl.K, None, y=y, zf=zf)
+    g = graph_of(call)
+    for _ in range(5):
+        g.replay()
+    torch.cuda.synchronize()
+    ms = replay_ms(g, steps)
+    return {"workload": wl.name, "samples": wl.total, "latency_us": ms * 1e3,
+            "value": wl.total / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+            "step": "sos_filter (prepare + apply), one CUDA-graph replay"}, \
+        [ParityJob("lowpass", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), None, y, 1e-5)]
+
+
 def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
     """4096 channels, lengths U[2^10, 2^20], K U{1..8}, random sections,
-    nonzero zi: one prepare + apply per step, inputs resident."""
+    nonzero zi: one prepare + apply per step, captured as one CUDA graph and
+    replayed, inputs resident (8.5 GB, far beyond L2)."""
     import torch
     from synth import workloads
     from paper_2607_14054_gb300.autotune import autotune
@@ -333,18 +441,17 @@ def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
     plan = P.SosFilter(wl.lengths, wl.kmax, tuning=tuning, device=dev)
     y = torch.empty_like(wl.x)
     zf = torch.empty(wl.n_channels, wl.kmax, 2, device=dev)
-    for _ in range(2):
+
+    def call():
         plan(wl.x, wl.sos, wl.K, wl.zi, y=y, zf=zf)
+    call()
+    g = graph_of(call)
+    g.replay()
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        plan(wl.x, wl.sos, wl.K, wl.zi, y=y, zf=zf)
-    e1.record()
-    torch.cuda.synchronize()
+    ms = reduce_max(replay_ms(g, steps), world)
     if plan.device_status() != 0:
         raise RuntimeError("batched leg: device status")
-    ms = reduce_max(e0.elapsed_time(e1) / steps, world)
+    ext = plan.plan_extended()
     total = wl.total
     lens = wl.lengths.double()
     fma = float((lens * (6 * wl.K.cpu().double() + 1)).sum())
@@ -352,32 +459,20 @@ def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
     t_alu = fma / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
     roof = total / max(t_hbm, t_alu) / 1e9
     value = total * world / (ms * 1e-3) / 1e9
-    off = torch.cat([torch.zeros(1, dtype=torch.int64), torch.cumsum(wl.lengths, 0)])
-    checks = []
-    for c in range(0, wl.n_channels, 64):
-        a = int(off[c])
-        n = min(int(wl.lengths[c]), 1 << 16)
-        k = int(wl.K[c])
-        checks.append(("batched", wl.x[a:a + n].cpu(), wl.sos[c, :k].cpu(),
-                       wl.zi[c, :k].cpu(), y[a:a + n].cpu(), 1e-5))
     return {"workload": wl.name, "channels": wl.n_channels, "samples": total,
             "value": value, "unit": "Gsamples/s", "ms_per_step": ms,
             "roofline_gsamples_per_s": roof, "frac_of_roofline": value / world / roof,
             "bound": "hbm" if t_hbm >= t_alu else "alu", "tuning": list(tuning),
-            "step": "sos_filter (prepare + apply)"}, checks
-
-
-# the precision-stress channels' bound relative to the sample-by-sample FP32
-# recursion's own error (the block method rounds at more places: the lane
-# scan, the fold, the particular and the re-run)
-STRESS_FP32_FACTOR = 8.0
+            "precision_classes": {str(v): int((ext == v).sum()) for v in range(4)},
+            "step": "sos_filter (prepare + apply), one CUDA-graph replay"}, \
+        [ParityJob("batched", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), wl.zi, y, 1e-5)]
 
 
 def stress_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 3):
     """Precision stress: 64 x 2^26 samples, K = 8, poles at radius
     0.999..0.9999 (long memory horizons, per-channel segments), autotuned
-    (untimed), one prepare + apply per step.  Returns the leg's figures and the first 2^16 outputs of
-    every channel (causal prefixes) for the oracle check."""
+    (untimed), one prepare + apply per step.  Parity: every channel in full
+    and in 8 windows, each against the oracle run from the channel's start."""
     import torch
     from synth import workloads
     wl = workloads.precision_stress(device=dev)
@@ -397,12 +492,8 @@ def stress_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 3):
     if plan.device_status() != 0:
         raise RuntimeError("stress leg: device status")
     ms = reduce_max(e0.elapsed_time(e1) / steps, world)
-    hz, _ = plan.plan_info()
+    hz, segs = plan.plan_info()
     ext = plan.plan_extended()
-    L = int(wl.lengths[0])
-    n = 1 << 16
-    checks = [("stress", wl.x[c * L:c * L + n].cpu(), wl.sos[c].cpu(), None,
-               y[c * L:c * L + n].cpu(), 1e-3, STRESS_FP32_FACTOR) for c in range(wl.n_channels)]
     total = wl.total
     fma = 49.0 * total
     t_hbm = 8.0 * total / (hbm_gbs * 1e9)
@@ -412,13 +503,24 @@ def stress_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 3):
     return {"workload": wl.name, "channels": wl.n_channels, "samples": total,
             "value": value, "unit": "Gsamples/s", "ms_per_step": ms,
             "roofline_gsamples_per_s": roof, "frac_of_roofline": value / world / roof,
-            "carried_channels": int((hz < 0).sum()),
-            "extended_precision_channels": int(ext.sum()),
-            "tuning": list(plan.tuning), "step": "sos_filter (prepare + apply)"}, checks
+            "carried_channels": int((hz < 0).sum()), "min_segments_per_channel": int(segs.min()),
+            "precision_classes": {str(v): int((ext == v).sum()) for v in range(4)},
+            "tuning": list(plan.tuning), "step": "sos_filter (prepare + apply)"}, \
+        [ParityJob("stress", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), None, y, 1e-3,
+                   windows=8, chunk=8)]
 
 
-def backward_leg(P, dev, world, steps: int = 5):
-    """256 x 2^16, K = 8: forward + backward through the autograd Function."""
+# backward FMAs per sample and section, the count of the method's adjoint:
+# 6 to recompute the section's input (forward), 6 for the adjoint run
+# (all-pole and FIR parts of the transposed recurrence), 5 for the
+# coefficient sums; bytes per sample: x and dL/dy read, dL/dx written
+BWD_FMA_PER_SECTION = 17
+BWD_BYTES_PER_SAMPLE = 12
+
+
+def backward_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
+    """256 x 2^16, K = 8: forward + backward through the autograd Function;
+    the backward launch alone is also timed for its roofline."""
     import torch
     from synth import workloads
     wl = workloads.differentiation(device=dev)
@@ -442,9 +544,34 @@ def backward_leg(P, dev, world, steps: int = 5):
     e1.record()
     torch.cuda.synchronize()
     ms = reduce_max(e0.elapsed_time(e1) / steps, world)
-    return {"workload": wl.name, "samples": wl.total,
-            "value": wl.total * world / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-            "ms_per_step": ms, "step": "forward + MSE + backward (dL/dx, dL/dsos, dL/dzi)"}
+    # the library's backward call alone (plan, adjoint kernel, finalize)
+    plan = P.SosFilter(wl.lengths, wl.kmax, device=dev)
+    gy = torch.randn_like(wl.x)
+    plan.backward(wl.x, wl.sos, wl.K, wl.zi, gy)
+
+    def bwd():
+        plan.backward(wl.x, wl.sos, wl.K, wl.zi, gy)
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for _ in range(steps):
+        bwd()
+    b1.record()
+    torch.cuda.synchronize()
+    ms_b = reduce_max(b0.elapsed_time(b1) / steps, world)
+    total = wl.total
+    fmas = BWD_FMA_PER_SECTION * float((wl.lengths.double() * wl.K.cpu().double()).sum())
+    t_alu = fmas / (sms * FP32_LANES_PER_SM * sm_max * 1e6)
+    t_hbm = BWD_BYTES_PER_SAMPLE * total / (hbm_gbs * 1e9)
+    roof = total / max(t_alu, t_hbm) / 1e9
+    vb = total * world / (ms_b * 1e-3) / 1e9
+    return {"workload": wl.name, "samples": total,
+            "value": total * world / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+            "ms_per_step": ms, "step": "forward + MSE + backward (dL/dx, dL/dsos, dL/dzi)",
+            "backward_call": {"ms": ms_b, "value": vb, "unit": "Gsamples/s",
+                              "roofline_gsamples_per_s": roof, "frac_of_roofline": vb / world / roof,
+                              "bound": "alu" if t_alu >= t_hbm else "hbm",
+                              "fma_per_sample_section": BWD_FMA_PER_SECTION}}
 
 
 def main():
@@ -459,8 +586,8 @@ def main():
     ap.add_argument("--clock-seconds", type=float, default=2.0)
     ap.add_argument("--clocks-out", default="")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the batched and differentiation legs")
-    ap.add_argument("--leg", default="", choices=["", "backward"],
+                    help="skip the low-pass, batched, differentiation and stress legs")
+    ap.add_argument("--leg", default="", choices=["", "backward", "batched", "stress"],
                     help="run only this extra leg and print its figures (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -474,9 +601,16 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2607_14054_gb300 as P
     from synth import workloads
+    peaks, src = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
 
-    if args.leg == "backward":
-        line = {"leg": "backward", **backward_leg(P, dev, world, steps=args.steps)}
+    if args.leg:
+        fn = {"backward": lambda: backward_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps),
+              "batched": lambda: batched_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps)[0],
+              "stress": lambda: stress_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps)[0]}
+        line = {"leg": args.leg, **fn[args.leg]()}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return 0
@@ -489,6 +623,10 @@ def main():
         from paper_2607_14054_gb300.autotune import autotune
         tuning = autotune(wl.x, wl.sos, wl.K, wl.lengths, None)
     plan = P.SosFilter(wl.lengths, Kmax, tuning=tuning, device=dev)
+    # the same tuning with the plan cache off: every step recomputes the
+    # tables (the cost of a call whose coefficients changed)
+    tr = list(tuning) + [0] * (4 - len(tuning))
+    plan_re = P.SosFilter(wl.lengths, Kmax, tuning=(tr[0], tr[1], tr[2], tr[3] | 8), device=dev)
     x = wl.x
     sos = wl.sos
     K = wl.K
@@ -504,35 +642,23 @@ def main():
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    # each half of the step is replayed from a captured CUDA graph (one launch
-    # each), so the timed region holds no host-side launch gaps
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(side):
-        step()
-    torch.cuda.current_stream(dev).wait_stream(side)
-    # the step as one captured CUDA graph: sos_prepare (the plan kernel), then
-    # sos_apply (the horizon kernel launched early behind the plan, the
-    # look-back kernel launched early behind it); each half and the horizon
-    # kernel alone are captured too and timed in loops of their own for the
-    # breakdown and the roofline
-    g_step, g_prep, g_apply, g_pipe = (torch.cuda.CUDAGraph() for _ in range(4))
-    with torch.cuda.graph(g_step):
-        plan.prepare(sos, K)
-        plan.apply(x, y, None, zf)
-    with torch.cuda.graph(g_prep):
-        plan.prepare(sos, K)
-    with torch.cuda.graph(g_apply):
-        plan.apply(x, y, None, zf)
-    with torch.cuda.graph(g_pipe):
-        plan.apply_part("pipeline", x, y, None, zf)
-    torch.cuda.synchronize()
-
-    def step():  # noqa: F811 - the captured form of the same step
-        g_step.replay()
+    # the step as one captured CUDA graph: sos_prepare (the plan kernel; the
+    # coefficients are those of the previous step, so the plan cache keeps the
+    # tables after checking them on the device), then sos_apply (the horizon
+    # kernel launched early behind the plan, the look-back kernel launched
+    # early behind it); the same step with the cache off, each half, and the
+    # horizon kernel alone are captured too and timed in loops of their own
+    g_step = graph_of(step)
+    g_replan = graph_of(lambda: (plan_re.prepare(sos, K), plan_re.apply(x, y, None, zf)))
+    g_prep = graph_of(lambda: plan.prepare(sos, K))
+    g_prep_re = graph_of(lambda: plan_re.prepare(sos, K))
+    g_apply = graph_of(lambda: plan.apply(x, y, None, zf))
+    g_pipe = graph_of(lambda: plan.apply_part("pipeline", x, y, None, zf))
     st = plan.device_status()
     if st != 0:
         raise RuntimeError(f"device status {st} after warm-up")
+    if plan.plan_recomputed() != 0:
+        raise RuntimeError("the plan cache did not keep the tables")
 
     stream = torch.cuda.current_stream(dev)
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
@@ -547,25 +673,13 @@ def main():
     torch.cuda.synchronize()
     barrier(world)
     t_wall = time.perf_counter() - t_wall0
-
-    def loop_ms(g):
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
-        for i in range(args.steps):
-            flush.zero_()
-            evs[i][0].record(stream)
-            g.replay()
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
-        return [e[0].elapsed_time(e[1]) for e in evs]
-    pipe_ms = loop_ms(g_pipe)
-    prep_ms = loop_ms(g_prep)
-    apply_ms = loop_ms(g_apply)
     step_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    ms_per_step = sum(step_ms) / len(step_ms)
-    ms_apply = sum(apply_ms) / len(apply_ms)
-    ms_pipe = reduce_max(sum(pipe_ms) / len(pipe_ms), world)
-    ms_per_step = reduce_max(ms_per_step, world)
-    ms_apply = reduce_max(ms_apply, world)
+    ms_per_step = reduce_max(sum(step_ms) / len(step_ms), world)
+    ms_pipe = reduce_max(replay_ms(g_pipe, args.steps, flush), world)
+    ms_prep = replay_ms(g_prep, args.steps, flush)
+    ms_prep_re = replay_ms(g_prep_re, args.steps, flush)
+    ms_apply = reduce_max(replay_ms(g_apply, args.steps, flush), world)
+    ms_replan = reduce_max(replay_ms(g_replan, args.steps, flush), world)
     samples = wl.total
     value = samples * world / (ms_per_step * 1e-3) / 1e9
 
@@ -579,40 +693,50 @@ def main():
         while time.perf_counter() - t0 < args.clock_seconds:
             for _ in range(50):
                 flush.zero_()
-                step()
+                g_step.replay()
             torch.cuda.synchronize()
         clocks = sampler.stop()
 
     # end to end through the public API: pinned host input -> device ->
-    # filter -> host output, every step
-    e2e_value, e2e_ms = None, None
+    # filter -> host output, every step; beside it the box's own pinned copy
+    # rates, whose sum of both directions bounds it
+    e2e = None
     if not args.no_e2e:
         e2e_value, e2e_ms = end_to_end(P, x, sos, stream, samples, world, args, plan.tuning)
+        rates = copy_rates(x, stream)
+        copy_ms = 4 * samples / (rates["h2d"] * 1e9) * 1e3 + 4 * samples / (rates["d2h"] * 1e9) * 1e3
+        copy_bound = samples / (copy_ms * 1e-3) / 1e9
+        e2e = {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
+               "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
+               "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)",
+               "copy_gbs": {"h2d": rates["h2d"], "d2h": rates["d2h"]},
+               "copy_bound_gsamples_per_s": copy_bound,
+               "frac_of_copy_bound": e2e_value / world / copy_bound,
+               "copy_bound_note": "input copied in and output copied out once per step at the "
+                                  "box's measured pinned rates, nothing else"}
 
-    # causal prefix of the output for the oracle check of the cpu_baseline leg
-    checks = [("bandpass16", x[:1 << 20].cpu(), sos[0].cpu(), None, y[:1 << 20].cpu(), 1e-5)]
+    jobs = [ParityJob("bandpass16", x, sos.cpu(), K.cpu(), wl.lengths.numpy(), None, y, 1e-5)]
 
-    peaks, src = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     fmas = fma_per_sample(8)
+    peak_tflops = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
     achieved = 2.0 * fmas * samples / (ms_pipe * 1e-3) / 1e12
     kname = horizon_kernel(plan.tuning)
     traffic = profiled_traffic(kname, samples)
-    hbm_gbs = float(peaks.get("hbm_gbs", 6800.0))
     roof_samples = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / fmas) / 1e9
 
-    batched = backward = stress = None
+    lowpass = batched = backward = stress = None
     if not args.no_extra:
-        batched, c_b = batched_leg(P, dev, world, sms, sm_max, hbm_gbs)
-        backward = backward_leg(P, dev, world)
-        stress, c_s = stress_leg(P, dev, world, sms, sm_max, hbm_gbs)
-        checks += c_b + c_s
+        lowpass, j = lowpass_leg(P, dev)
+        jobs += j
+        batched, j = batched_leg(P, dev, world, sms, sm_max, hbm_gbs)
+        jobs += j
+        backward = backward_leg(P, dev, world, sms, sm_max, hbm_gbs)
+        stress, j = stress_leg(P, dev, world, sms, sm_max, hbm_gbs)
+        jobs += j
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = oracle_baseline(workloads.plain_bandpass16(n=1 << 24, device="cpu"), checks=checks)
+        cpu = oracle_baseline(workloads.plain_bandpass16(n=1 << 24, device="cpu"), jobs=jobs)
 
     line = {
         "metric": "Gsamples/s K=8 FP32 (batched/plain) and % roofline at rel-L2<=1e-5 vs FP64",
@@ -631,12 +755,17 @@ def main():
                    "parallelism": f"replicas{world}", "l2": "flushed between steps (256 MiB write)",
                    "tuning": list(plan.tuning),
                    "tuning_source": "--tuning" if args.tuning else "autotuner (untimed setup)",
-                   "step": "sos_prepare + sos_apply (one CUDA-graph replay: plan kernel, "
-                           "horizon kernel launched early behind it, look-back kernel "
-                           "launched early behind that)",
-                   "breakdown": "ms_prepare, ms_apply, ms_horizon_kernel: each part "
-                                "replayed alone in a loop of its own",
-                   "ms_prepare": sum(prep_ms) / len(prep_ms), "ms_apply": ms_apply,
+                   "step": "sos_filter on a new signal with the same filter: sos_prepare (plan "
+                           "kernel; the plan cache keeps the tables after comparing the "
+                           "coefficients on the device) + sos_apply (horizon kernel launched "
+                           "early behind the plan, look-back kernel early behind that), one "
+                           "CUDA-graph replay",
+                   "headline": "ms_per_step (plan cache on)",
+                   "breakdown": "ms_prepare, ms_apply, ms_horizon_kernel, ms_step_replan, "
+                                "ms_prepare_replan: each replayed alone in a loop of its own",
+                   "ms_prepare": ms_prep, "ms_apply": ms_apply,
+                   "ms_step_replan": ms_replan, "ms_prepare_replan": ms_prep_re,
+                   "value_replan": samples * world / (ms_replan * 1e-3) / 1e9,
                    "horizon_kernel": kname, "ms_horizon_kernel": ms_pipe,
                    "roofline_gsamples_per_s": roof_samples,
                    "frac_of_sample_roofline": value / world / roof_samples,
@@ -646,11 +775,9 @@ def main():
                      "kernel": kname, "flops_per_sample": 2 * fmas,
                      "peak_source": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                                     f"{sm_max:.0f} MHz ({src} max clock)"},
-        "e2e": None if e2e_value is None else {
-            "value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 4 * samples,
-            "d2h_bytes_per_step": 4 * samples, "ms_per_step": e2e_ms,
-            "api": "paper_2607_14054_gb300.sosfilt (pinned host buffers)"},
+        "e2e": e2e,
         "gpu_launches": 3 * args.steps,
+        "lowpass": lowpass,
         "batched": batched,
         "backward": backward,
         "stress": stress,

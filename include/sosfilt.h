@@ -325,6 +325,18 @@ sos_status sos_plan_query(void *workspace, int32_t first, int32_t count, int32_t
 sos_status sos_plan_extended(void *workspace, int32_t first, int32_t count, int32_t *extended,
                              void *stream);
 
+/* Sets the bound on every device-side wait of later calls on this workspace
+ * (the look-back's polls for a predecessor tile's state, the hand-overs
+ * between the warps of one CTA): `limit` polls, or the compiled default for
+ * 0 (sos_workspace_init also restores the default).  A wait that runs out
+ * records SOS_ERR_TIMEOUT in the workspace's status word and the kernel
+ * carries on with what it has (wrong values, but every access stays in
+ * bounds and the kernel completes), so that a hung predecessor cannot hang
+ * the GPU; a small limit lets a caller test that path.  The copy is ordered
+ * on `stream` and waited for, so not for use during a stream capture.  No
+ * counterpart in the paper. */
+sos_status sos_workspace_set_wait_limit(void *workspace, uint32_t limit, void *stream);
+
 /* Waits for `stream`, then writes into *channels the number of channels
  * whose tables the most recent sos_prepare on this workspace recomputed (0:
  * every channel's tables and the dispatch order came from the plan cache;

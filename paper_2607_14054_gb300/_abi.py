@@ -99,6 +99,8 @@ def load(build_if_missing: bool = False):
         lib.sos_plan_query.restype = ctypes.c_int
         lib.sos_plan_extended.argtypes = [vp, i32, i32, vp, vp]
         lib.sos_plan_extended.restype = ctypes.c_int
+        lib.sos_workspace_set_wait_limit.argtypes = [vp, ctypes.c_uint32, vp]
+        lib.sos_workspace_set_wait_limit.restype = ctypes.c_int
         lib.sos_plan_recomputed.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), vp]
         lib.sos_plan_recomputed.restype = ctypes.c_int
         _lib = lib
@@ -201,6 +203,11 @@ def sos_plan_extended(ws_ptr: int, first: int, count: int, extended_ptr: int,
     """Host pointer as an integer."""
     V = ctypes.c_void_p
     return int(load().sos_plan_extended(V(ws_ptr), first, count, V(extended_ptr), V(stream)))
+
+
+def sos_workspace_set_wait_limit(ws_ptr: int, limit: int, stream: int) -> int:
+    return int(load().sos_workspace_set_wait_limit(ctypes.c_void_p(ws_ptr), int(limit),
+                                                   ctypes.c_void_p(stream)))
 
 
 def sos_plan_recomputed(ws_ptr: int, stream: int):

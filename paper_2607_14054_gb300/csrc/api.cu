@@ -385,6 +385,18 @@ sos_status sos_plan_extended(void* workspace, int32_t first, int32_t count, int3
     return SOS_OK;
 }
 
+sos_status sos_workspace_set_wait_limit(void* workspace, uint32_t limit, void* stream) {
+    if (!workspace) return SOS_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const uint32_t v = limit;
+    if (cudaMemcpyAsync(&static_cast<WsHeader*>(workspace)->spin_limit, &v, sizeof(v),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    // the source is a local: the copy must have read it before returning
+    if (cudaStreamSynchronize(st) != cudaSuccess) return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
 sos_status sos_plan_recomputed(void* workspace, int32_t* channels, void* stream) {
     if (!workspace || !channels) return SOS_ERR_ARG;
     if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess)

@@ -237,10 +237,11 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
         if (warp > 0) {
             // bounded wait for the predecessor warp's hand-off
             unsigned long long* b = &ho->bar[k][warp - 1];
+            const uint32_t limit = wait_limit(p.hdr, kHandOffLimit);
             for (uint32_t it = 0;; ++it) {
                 const bool ok = mbar_try_wait(b, par);
                 if (__all_sync(0xffffffffu, ok)) break;
-                if (it >= kHandOffLimit) {
+                if (it >= limit) {
                     if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
                     break;
                 }

@@ -137,6 +137,7 @@ __device__ void lookback_warp(const Params& p, int64_t t, int64_t npred, int k, 
     int64_t base = REV ? t + 1 : t - 1;
     int64_t remaining = npred;
     uint32_t spins = 0;
+    const uint32_t limit = wait_limit(p.hdr, kSpinLimit);
     for (;;) {
         const int cnt = (int)(remaining < WIN ? remaining : WIN);
         df i1[R], i2[R];
@@ -240,7 +241,7 @@ __device__ void lookback_warp(const Params& p, int64_t t, int64_t npred, int k, 
                 break;  // continue WIN tiles further back
             }
             ++spins;
-            if (spins > kSpinLimit) {
+            if (spins > limit) {
                 if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
                 Z1 = acc1;
                 Z2 = acc2;

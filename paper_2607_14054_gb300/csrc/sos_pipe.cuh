@@ -58,10 +58,11 @@ struct PipeShared {
 // Bounded, warp-uniform wait for an mbarrier phase.
 __device__ __forceinline__ void pipe_wait(const Params& p, unsigned long long* b, unsigned par,
                                           int lane) {
+    const uint32_t limit = wait_limit(p.hdr, kHandOffLimit);
     for (uint32_t it = 0;; ++it) {
         const bool ok = mbar_try_wait(b, par);
         if (__all_sync(0xffffffffu, ok)) return;
-        if (it >= kHandOffLimit) {
+        if (it >= limit) {
             if (lane == 0) set_status(p.hdr, SOS_ERR_TIMEOUT);
             return;
         }

@@ -1,6 +1,6 @@
-"""The bench's oracle-parity aggregation (cpu_baseline leg), on the CPU:
-per-check relative L2 against the oracle, counts within tolerance, and the
-optional bound relative to the sample-by-sample FP32 recursion."""
+"""The bench's oracle-parity jobs (cpu_baseline leg), on the CPU: per-channel
+relative L2 against the oracle over whole channels and windows, counts within
+tolerance."""
 import numpy as np
 import torch
 
@@ -9,22 +9,30 @@ import oracle
 from synth import workloads
 
 
-def test_parity_aggregation_and_fp32_bound():
-    wl = workloads.plain_lowpass(n=4096)
-    x, sos = wl.x, wl.sos[0]
-    ref, _ = oracle.sosfilt(x.double().numpy(), sos.numpy())
+def test_parity_jobs_whole_channels_and_windows():
+    wl = workloads.batched(n_channels=5, min_len=3000, max_len=9000, seed=9)
+    ref, _ = oracle.sosfilt(wl.x.double().numpy(), wl.sos.numpy(), K=wl.K.numpy(),
+                            lengths=wl.lengths.numpy(), zi=wl.zi.double().numpy())
     exact = torch.from_numpy(ref.astype(np.float32))
-    off = torch.from_numpy((ref * 1.01).astype(np.float32))  # 1e-2 relative
-    checks = [("a", x, sos, None, exact, 1e-5), ("a", x, sos, None, off, 1e-5),
-              ("b", x, sos, None, off, 1e-3, 8.0), ("b", x, sos, None, exact, 1e-3, 8.0)]
-    out = bench.oracle_baseline(wl, target_seconds=0.01, checks=checks)
+    off = np.concatenate([[0], np.cumsum(wl.lengths.numpy())])
+    bad = exact.clone()
+    c = 3
+    n = int(wl.lengths[c])
+    # channel 3: its last fifth 1 % off (whole-channel error below 1 %)
+    bad[off[c] + n - n // 5:off[c + 1]] *= 1.01
+    jobs = [bench.ParityJob("ok", wl.x, wl.sos, wl.K, wl.lengths.numpy(), wl.zi, exact, 1e-5,
+                            windows=5, chunk=2),
+            bench.ParityJob("bad", wl.x, wl.sos, wl.K, wl.lengths.numpy(), wl.zi, bad, 1e-3,
+                            windows=5, chunk=3),
+            bench.ParityJob("some", wl.x, wl.sos, wl.K, wl.lengths.numpy(), wl.zi, bad, 1e-3,
+                            channels=[0, 3])]
+    out = bench.oracle_baseline(wl, target_seconds=0.01, jobs=jobs)
     assert out["kind"] == "oracle" and out["value"] > 0
-    a, b = out["parity"]["a"], out["parity"]["b"]
-    assert a["channels"] == 2 and a["samples"] == 2 * 4096
-    assert a["within_tolerance"] == 1 and abs(a["rel_l2"] - 1e-2) < 1e-5
-    assert "within_fp32_bound" not in a
-    # the FP32 recursion is far below 1e-3 on this filter, so the bound is the
-    # tolerance itself: the 1e-2 output is 10x over it, the exact one within
-    assert b["fp32_factor"] == 8.0 and 0 < b["fp32_sequential_rel_l2"] < 1e-5
-    assert b["within_fp32_bound"] == 1 and b["within_tolerance"] == 1
-    assert abs(b["worst_error_over_bound"] - 10.0) < 1e-2
+    ok, b, some = out["parity"]["ok"], out["parity"]["bad"], out["parity"]["some"]
+    assert ok["channels"] == 5 and ok["samples"] == int(wl.lengths.sum())
+    assert ok["within_tolerance"] == 5 and ok["within_tolerance_every_window"] == 5
+    assert ok["rel_l2"] < 1e-6 and ok["worst_window_rel_l2"] < 1e-6
+    # the windows catch what the whole-channel error may average away
+    assert b["within_tolerance_every_window"] == 4 and b["within_tolerance"] >= 4
+    assert abs(b["worst_window_rel_l2"] - 1e-2) < 1e-4
+    assert some["channels"] == 2 and some["rel_l2"] > 1e-4

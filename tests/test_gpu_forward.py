@@ -463,3 +463,36 @@ def test_lookback_long_memory_every_tile():
                 a, b = t * T, (t + 1) * T
                 err = np.linalg.norm(got[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
                 assert err <= 1e-3, (tuning, c, t, err)
+
+
+def test_bounded_wait_runs_out_and_the_workspace_recovers():
+    """The look-back's polls for a predecessor tile are bounded.  With the
+    bound set to one poll, tiles of a long carried channel whose predecessor
+    has not published yet give up: the call reports SOS_ERR_TIMEOUT (every
+    predecessor still publishes, so nothing waits forever, and the kernel
+    completes).  With the default bound restored, the next call on the same
+    workspace reports SOS_OK and matches the oracle."""
+    P = _lib()
+    n = 1 << 22
+    args = random_case(77, [n], 8, rmax=0.99)
+    x, sos, K, L, zi = (a.cuda() if a is not None and a.dtype != torch.int64 else a for a in args)
+    plan = P.SosFilter(L, 8, tuning=(32, 8, 1, P._abi.SOS_FLAG_CARRY_ONLY))
+    stream = torch.cuda.current_stream().cuda_stream
+    y0, _ = plan(x, sos, K, zi)
+    assert plan.device_status() == 0
+    assert P._abi.sos_workspace_set_wait_limit(plan.workspace.data_ptr(), 1, stream) == 0
+    timed_out = False
+    for _ in range(5):
+        plan(x, sos, K, zi)
+        st = plan.device_status()
+        assert st in (0, -4), st
+        if st == -4:
+            timed_out = True
+            break
+    assert timed_out
+    assert P._abi.sos_workspace_set_wait_limit(plan.workspace.data_ptr(), 0, stream) == 0
+    y, zf = plan(x, sos, K, zi)
+    assert plan.device_status() == 0
+    y_ref, zf_ref = run_oracle(*args)
+    check(y.cpu().numpy(), zf.cpu().numpy(), y_ref, zf_ref, L.numpy(), K.cpu().numpy(), 1e-5)
+    assert torch.equal(y, y0)
