@@ -139,6 +139,7 @@ template <int W>
 struct HandOff {
     float2 val[kMaxSections][W];
     unsigned long long bar[kMaxSections][W];
+    uint32_t limit;  // bound on each hand-off wait (polls), read once per launch
 };
 
 
@@ -237,7 +238,7 @@ __device__ __forceinline__ void data_section(const Params& p, float (&v)[N], int
         if (warp > 0) {
             // bounded wait for the predecessor warp's hand-off
             unsigned long long* b = &ho->bar[k][warp - 1];
-            const uint32_t limit = wait_limit(p.hdr, kHandOffLimit);
+            const uint32_t limit = ho->limit;
             for (uint32_t it = 0;; ++it) {
                 const bool ok = mbar_try_wait(b, par);
                 if (__all_sync(0xffffffffu, ok)) break;
@@ -395,6 +396,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sos_forward_kernel(Params 
     const int64_t nrounds = p.hdr->nrounds;
     // hand-off barriers (made visible to the CTA by the first loop barrier)
     for (int i = tid; i < kMaxSections * W; i += blockDim.x) mbar_init(&ho.bar[0][0] + i, 1);
+    if (tid == 0) ho.limit = wait_limit(p.hdr, kHandOffLimit);
     uint32_t ph = 0;  // data warps: hand-off barrier parity per section
 
     // final states that no tile writes: sections past K[c] are zero, an

@@ -65,7 +65,7 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
     // holds none of the zf selects
     auto group = [&](int g, auto zg) {
         constexpr bool ZG = decltype(zg)::value;
-        pipe_wait(p, &sh.bar[s][k], use & 1u, lane);
+        pipe_wait(p, &sh.bar[s][k], use & 1u, lane, sh.limit);
         float* row = ring + s * SL::kFloats + lane * SL::kRow;
         const bool zf_owner = ZG && lane == owner;
         float v[N];
@@ -125,6 +125,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
         for (int j = 0; j < kPipeStages; ++j) mbar_init(&sh.bar[i][j], 32);
         mbar_init(&sh.free_[i], 32);
     }
+    if (tid == 0) sh.limit = wait_limit(p.hdr, kHandOffLimit);
     __syncthreads();
 
     // ring position of the next group (all warps walk the same sequence):
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
             const float* src = p.x + sg.off + sg.cstart;
             int rem = (int)(sg.len - sg.cstart < 0x40000000 ? sg.len - sg.cstart : 0x40000000);
             for (int g = 0; g < sg.ngroups; ++g, src += PC::kGroup, rem -= PC::kGroup) {
-                if (use > 0) pipe_wait(p, &sh.free_[s], (use - 1) & 1u, lane);
+                if (use > 0) pipe_wait(p, &sh.free_[s], (use - 1) & 1u, lane, sh.limit);
                 float* slot = ring + s * SL::kFloats;
                 if (rem >= PC::kGroup && ((reinterpret_cast<uintptr_t>(src) & 15u) == 0)) {
                     const float4* s4 = reinterpret_cast<const float4*>(src);
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
             int b = (int)(sg.out_hi - sg.cstart);
             for (int g = 0; g < sg.ngroups; ++g, dst += PC::kGroup, a -= PC::kGroup,
                      b -= PC::kGroup) {
-                pipe_wait(p, &sh.bar[s][kMaxSections], use & 1u, lane);
+                pipe_wait(p, &sh.bar[s][kMaxSections], use & 1u, lane, sh.limit);
                 const float* slot = ring + s * SL::kFloats;
                 const int lo = a > 0 ? a : 0;
                 const int hi = b < PC::kGroup ? b : PC::kGroup;
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
             } else {
                 // past the channel's K: pass the groups through
                 for (int g = 0; g < sg.ngroups; ++g) {
-                    pipe_wait(p, &sh.bar[s][k], use & 1u, lane);
+                    pipe_wait(p, &sh.bar[s][k], use & 1u, lane, sh.limit);
                     pipe_arrive(&sh.bar[s][k + 1]);
                     if (++s == kPipeRing) {
                         s = 0;

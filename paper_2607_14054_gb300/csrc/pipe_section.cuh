@@ -205,56 +205,86 @@ struct SecDF {
     df a1, a2, b0, b1, b2;
 };
 
-// One section over one group with the samples themselves in double-float
-// (chunk vh[] + vl[]): the same steps as pipe_section -- S3 with zero in-lane
-// history, S4 (i) the particular solution's terminal pair, (ii) the lane scan
-// and the fold of the group's incoming state, (iii) the re-run from the true
-// lane state, the group's outgoing state, S8 -- every one in double-float
-// (about 44 bits), so that neither the samples handed from section to section
-// nor the recursions' own roundings are limited to FP32.  For cascades in
-// which later sections attenuate what earlier ones pass (poles next to the
-// unit circle), where FP32 rounding of an intermediate signal reaches the
-// output amplified many times.  Z1, Z2: the group's incoming DF2T state, left
-// outgoing.  ZF: the group holds the channel's last sample (element mq of the
-// chunk of the lane where zf_owner is set), whose state goes to zf_dst.
+// One section over one group with the samples themselves in double-float:
+// the high parts in the lane's chunk vh[] (registers), the low parts in the
+// lane's row lo[] (shared memory, 16-byte aligned, read and written four at
+// a time, which the row padding makes bank-conflict free; registers would
+// double the section's footprint).  The same steps as pipe_section -- S3 with
+// zero in-lane history, S4 (i) the particular solution's terminal pair, (ii)
+// the lane scan and the fold of the group's incoming state, (iii) the re-run
+// from the true lane state, the group's outgoing state, S8 -- every one in
+// double-float (about 44 bits), so that neither the samples handed from
+// section to section nor the recursions' own roundings are limited to FP32.
+// For cascades in which later sections attenuate what earlier ones pass
+// (poles next to the unit circle), where FP32 rounding of an intermediate
+// signal reaches the output amplified many times.  Z1, Z2: the group's
+// incoming DF2T state, left outgoing.  ZF: the group holds the channel's last
+// sample (element mq of the chunk of the lane where zf_owner is set), whose
+// state goes to zf_dst.
 template <int N, bool ZF = false>
-__device__ __forceinline__ void pipe_section_dfx(float (&vh)[N], float (&vl)[N], const SecDF& q,
+__device__ __forceinline__ void pipe_section_dfx(float (&vh)[N], float* lo, const SecDF& q,
                                                  const float4* phi, const float4* phi_lo,
                                                  const float4 lp, const float4 lpl, df& Z1,
                                                  df& Z2, bool zf_owner, int mq, float* zf_dst) {
     const int lane = threadIdx.x & 31;
     const df na1 = df_neg(q.a1);
+    float4* lo4 = reinterpret_cast<float4*>(lo);
     df xq{0.f, 0.f}, xqm1{0.f, 0.f};
     if (ZF) {
         pick_pair<N>(vh, mq, xq.hi, xqm1.hi);
-        pick_pair<N>(vl, mq, xq.lo, xqm1.lo);
+        xq.lo = lo[mq];
+        xqm1.lo = mq >= 1 ? lo[mq - 1] : 0.f;
     }
-    const df xl1{vh[N - 1], vl[N - 1]}, xl2{vh[N - 2], vl[N - 2]};
-    // S3, top down so that each step still sees the inputs it needs
+    const float4 top = lo4[N / 4 - 1];
+    const df xl1{vh[N - 1], top.w}, xl2{vh[N - 2], top.z};
+    // S3, top down (block q of four samples reads the inputs of blocks q and
+    // q - 1, which the steps below it have not overwritten yet)
 #pragma unroll
-    for (int m = N - 1; m >= 2; --m) {
-        const df u = df_dot3(q.b0, df{vh[m], vl[m]}, q.b1, df{vh[m - 1], vl[m - 1]}, q.b2,
-                             df{vh[m - 2], vl[m - 2]});
-        vh[m] = u.hi;
-        vl[m] = u.lo;
-    }
-    {
-        const df u1 = df_dot3(q.b0, df{vh[1], vl[1]}, q.b1, df{vh[0], vl[0]}, df{0.f, 0.f},
-                              df{0.f, 0.f});
-        const df u0 = df_mul(q.b0, df{vh[0], vl[0]});
-        vh[1] = u1.hi;
-        vl[1] = u1.lo;
-        vh[0] = u0.hi;
-        vl[0] = u0.lo;
+    for (int b = N / 4 - 1; b >= 0; --b) {
+        const float4 c = lo4[b];
+        const float4 d = b > 0 ? lo4[b > 0 ? b - 1 : 0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float l[6] = {d.z, d.w, c.x, c.y, c.z, c.w};  // lo of x_{4b-2} .. x_{4b+3}
+        float h[6];
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            const int m = 4 * b - 2 + i;
+            h[i] = m >= 0 ? vh[m >= 0 ? m : 0] : 0.f;
+        }
+        float out[4];
+#pragma unroll
+        for (int i = 3; i >= 0; --i) {
+            const int m = 4 * b + i;
+            df u;
+            if (m >= 2)
+                u = df_dot3(q.b0, df{h[i + 2], l[i + 2]}, q.b1, df{h[i + 1], l[i + 1]}, q.b2,
+                            df{h[i], l[i]});
+            else if (m == 1)
+                u = df_dot3(q.b0, df{h[i + 2], l[i + 2]}, q.b1, df{h[i + 1], l[i + 1]},
+                            df{0.f, 0.f}, df{0.f, 0.f});
+            else
+                u = df_mul(q.b0, df{h[i + 2], l[i + 2]});
+            vh[m] = u.hi;
+            out[i] = u.lo;
+        }
+        lo4[b] = make_float4(out[0], out[1], out[2], out[3]);
     }
     // S4 (i): the particular solution from zero state, its terminal pair
-    df w0{vh[0], vl[0]};
-    df w1 = df_rec1(df{vh[1], vl[1]}, q.a1, w0);
+    df w0{0.f, 0.f}, w1{0.f, 0.f};
 #pragma unroll
-    for (int m = 2; m < N; ++m) {
-        const df w2 = df_rec(df{vh[m], vl[m]}, q.a1, w1, q.a2, w0);
-        w0 = w1;
-        w1 = w2;
+    for (int b = 0; b < N / 4; ++b) {
+        const float4 c = lo4[b];
+        const float l[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = 4 * b + i;
+            const df u{vh[m], l[i]};
+            df w2;
+            if (m == 0) w2 = u;
+            else if (m == 1) w2 = df_rec1(u, q.a1, w1);
+            else w2 = df_rec(u, q.a1, w1, q.a2, w0);
+            w0 = w1;
+            w1 = w2;
+        }
     }
     df s1 = df_rec1(df_dot3(q.b1, xl1, q.b2, xl2, na1, w1), q.a2, w0);
     df s2 = df_rec1(df_mul(q.b2, xl1), q.a2, w1);
@@ -282,32 +312,38 @@ __device__ __forceinline__ void pipe_section_dfx(float (&vh)[N], float (&vl)[N],
     const df zin1 = df_add(e1, df_add(df_mul(df{lp.x, lpl.x}, Z1), df_mul(df{lp.y, lpl.y}, Z2)));
     const df zin2 = df_add(e2, df_add(df_mul(df{lp.z, lpl.z}, Z1), df_mul(df{lp.w, lpl.w}, Z2)));
     // S4 (iii): the re-run from the true lane state
-    {
-        const df y0 = df_add(df{vh[0], vl[0]}, zin1);
-        const df y1 = df_rec1(df_add(df{vh[1], vl[1]}, zin2), q.a1, y0);
-        vh[0] = y0.hi;
-        vl[0] = y0.lo;
-        vh[1] = y1.hi;
-        vl[1] = y1.lo;
-    }
+    df y1{0.f, 0.f}, y2{0.f, 0.f};  // y_{m-1}, y_{m-2}
 #pragma unroll
-    for (int m = 2; m < N; ++m) {
-        const df y = df_rec(df{vh[m], vl[m]}, q.a1, df{vh[m - 1], vl[m - 1]}, q.a2,
-                            df{vh[m - 2], vl[m - 2]});
-        vh[m] = y.hi;
-        vl[m] = y.lo;
+    for (int b = 0; b < N / 4; ++b) {
+        const float4 c = lo4[b];
+        const float l[4] = {c.x, c.y, c.z, c.w};
+        float out[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int m = 4 * b + i;
+            const df u{vh[m], l[i]};
+            df y;
+            if (m == 0) y = df_add(u, zin1);
+            else if (m == 1) y = df_rec1(df_add(u, zin2), q.a1, y1);
+            else y = df_rec(u, q.a1, y1, q.a2, y2);
+            vh[m] = y.hi;
+            out[i] = y.lo;
+            y2 = y1;
+            y1 = y;
+        }
+        lo4[b] = make_float4(out[0], out[1], out[2], out[3]);
     }
     // the group's outgoing state, from lane 31's last two inputs and outputs
-    const df yl1{vh[N - 1], vl[N - 1]}, yl2{vh[N - 2], vl[N - 2]};
-    const df o1 = df_rec1(df_dot3(q.b1, xl1, q.b2, xl2, na1, yl1), q.a2, yl2);
-    const df o2 = df_rec1(df_mul(q.b2, xl1), q.a2, yl1);
+    const df o1 = df_rec1(df_dot3(q.b1, xl1, q.b2, xl2, na1, y1), q.a2, y2);
+    const df o2 = df_rec1(df_mul(q.b2, xl1), q.a2, y1);
     Z1 = df{__shfl_sync(0xffffffffu, o1.hi, 31), __shfl_sync(0xffffffffu, o1.lo, 31)};
     Z2 = df{__shfl_sync(0xffffffffu, o2.hi, 31), __shfl_sync(0xffffffffu, o2.lo, 31)};
     // S8: final state at the channel's last sample
     if (ZF) {
         df yq, yqm1;
         pick_pair<N>(vh, mq, yq.hi, yqm1.hi);
-        pick_pair<N>(vl, mq, yq.lo, yqm1.lo);
+        yq.lo = lo[mq];
+        yqm1.lo = mq >= 1 ? lo[mq - 1] : 0.f;
         df f1;
         if (mq >= 1) f1 = df_rec1(df_dot3(q.b1, xq, q.b2, xqm1, na1, yq), q.a2, yqm1);
         else f1 = df_add(df_dot3(q.b1, xq, na1, yq, df{0.f, 0.f}, df{0.f, 0.f}), zin2);

@@ -402,7 +402,7 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
             ea += __shfl_xor_sync(0xffffffffu, ea, o);
         }
         E = fmaf(h0, h0, e);
-        return E > 0.f && E >= 1e-4f * ea && E < 1e30f;
+        return E > 0.f && E >= 1e-5f * ea && E < 1e30f;
     };
     float Epre[kMaxSections], Esuf[kMaxSections];
     bool ok = true;
@@ -851,7 +851,8 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         // the channel's precision class: the largest section level, or 3
         // (double-float samples) for a channel within its memory horizon
         // whose hand-off error estimate is too large (or unknown while some
-        // section is ill-conditioned), or when the call asks for it
+        // section needs the double-float scan), whose sections are
+        // ill-conditioned (kappa), or when the call asks for it
         int16_t e = 0;
         float kap = 0.f;
         for (int j = 0; j < Kc; ++j) {
@@ -860,7 +861,7 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         }
         const float h = s_handoff;
         const bool whole = (p.flags_opt & SOS_FLAG_DOUBLE_FLOAT) || h > kHandOffErrMax ||
-                           (h < 0.f && e > 0) || !(kap * 0x1p-24f <= kHandOffErrMax);
+                           (h < 0.f && e >= 2) || !(kap * 0x1p-24f <= kSectionErrMax);
         if (whole && s_horizon >= 0 && !(p.flags_opt & kFlagBackwardPlan)) e = 3;
         p.chan[c].ext = e;
     }

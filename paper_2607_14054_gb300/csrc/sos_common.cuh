@@ -152,15 +152,22 @@ constexpr double kAloCoefSens = 0x1p-18;
 // A channel is run with double-float samples throughout (ChanInfo::ext = 3)
 // when the relative error that FP32 rounding of the signals handed from one
 // section to the next would cause at the output, estimated by the plan for a
-// white input, exceeds kHandOffErrMax (or when the estimate cannot be formed
-// and some section is ill-conditioned), or when a section's own FP32
-// rounding is amplified beyond the same bound: rounding its FIR output or its
-// recursion adds white noise of relative size 2^-24, which its all-pole part
-// passes with gain ||g|| (g the all-pole impulse response) against a signal
-// passed with the whole section's gain ||h|| per unit ||b||, so the section's
-// condition number kappa = ||g|| ||b|| / ||h|| (zeros close to the poles make
-// it large) must stay below kHandOffErrMax * 2^24.
-constexpr float kHandOffErrMax = 0x1p-17f;
+// white input from zero state, exceeds kHandOffErrMax (or when the estimate
+// cannot be formed and some section needs the double-float scan), or when a
+// section's own FP32 rounding is amplified beyond kSectionErrMax: rounding
+// its FIR output or its recursion adds white noise of relative size 2^-24,
+// which its all-pole part passes with gain ||g|| (g the all-pole impulse
+// response) against a signal passed with the whole section's gain ||h|| per
+// unit ||b||, so the section's condition number kappa = ||g|| ||b|| / ||h||
+// (zeros close to the poles make it large) must stay below
+// kSectionErrMax * 2^24.  The measured error of the FP32 path is about 0.4 to
+// 30 times the hand-off estimate (the recursions' own roundings add to it);
+// kHandOffErrMax keeps the cascades whose estimate says FP32 cannot reach
+// about 1e-4 -- a white input from zero state through a random cascade near
+// the estimate's bound may still see errors of 1e-5..1e-4
+// (SOS_FLAG_DOUBLE_FLOAT removes them).
+constexpr float kHandOffErrMax = 0x1p-15f;
+constexpr float kSectionErrMax = 0x1p-17f;
 
 // Per (channel, section) double-float powers of the tile transition
 // Theta = A^T (T = tile length) for the cross-tile composition, each as

@@ -53,12 +53,13 @@ struct PipeShared {
     unsigned long long free_[kPipeRing];             // slot free for the loader
     float4 phi[kMaxSections][5];                     // section k's Phi^(2^j), staged by warp 1 + k
     float4 cr[kMaxSections][14];                     // section k's cyclic-reduction coefficients
+    uint32_t limit;                                  // bound on each hand-over wait (polls)
 };
 
 // Bounded, warp-uniform wait for an mbarrier phase.
+// (limit: the workspace's bound, read once per launch)
 __device__ __forceinline__ void pipe_wait(const Params& p, unsigned long long* b, unsigned par,
-                                          int lane) {
-    const uint32_t limit = wait_limit(p.hdr, kHandOffLimit);
+                                          int lane, uint32_t limit) {
     for (uint32_t it = 0;; ++it) {
         const bool ok = mbar_try_wait(b, par);
         if (__all_sync(0xffffffffu, ok)) return;

@@ -79,6 +79,42 @@ __device__ __forceinline__ SecDF load_secdf(const Coef32* cf) {
                  df{br.z, bl.z}};
 }
 
+// All K sections of a channel run with double-float samples over one group
+// (kPrecDF): on entry the lane's row holds its chunk of the group's FP32
+// input, on exit the chunk of the output, rounded once.  Out of line, so
+// that its register needs (a double-float section keeps several times the
+// temporaries of an FP32 one) do not reach the allocation of the FP32 code
+// in the same kernel; the call costs nothing next to the section's work.
+template <int N, bool ZF>
+__device__ __noinline__ void dfx_group(const Params& p, const Coef32* cf0, int K, int c,
+                                       float* row, float4* zs, int lane, int owner, int mq) {
+    float v[N];
+    row_to_chunk<N>(v, row);
+    // the low parts live in the lane's row; the input is FP32: they start at
+    // zero
+#pragma unroll
+    for (int b = 0; b < N / 4; ++b)
+        reinterpret_cast<float4*>(row)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 1
+    for (int k = 0; k < K; ++k) {
+        const Coef32* cf = cf0 + k;
+        const SecDF sd = load_secdf(cf);
+        const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane];
+        float* zf_dst = ZF ? p.zf + ((int64_t)c * p.kmax + k) * 2 : nullptr;
+        const float4 zz = zs[k];
+        df z1{zz.x, zz.y}, z2{zz.z, zz.w};
+        pipe_section_dfx<N, ZF>(v, row, sd, cf->phi_pow, cf->phi_lo, lp, lpl, z1, z2,
+                                lane == owner, mq, zf_dst);
+        if (lane == 0) zs[k] = make_float4(z1.hi, z1.lo, z2.hi, z2.lo);
+    }
+#pragma unroll
+    for (int b = 0; b < N / 4; ++b) {
+        const float4 l = reinterpret_cast<const float4*>(row)[b];
+        reinterpret_cast<float4*>(row)[b] = make_float4(v[4 * b + 0] + l.x, v[4 * b + 1] + l.y,
+                                                        v[4 * b + 2] + l.z, v[4 * b + 3] + l.w);
+    }
+}
+
 // One group of a segment through all K sections: prefetch the next group,
 // filter this one in registers, store the segment's own outputs.  ZF: the
 // group holding the channel's last sample, whose final state (zf) is taken at
@@ -111,28 +147,11 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
     float* slot = slots + cur * WC::kSlot;
     float* row = slot + lane * SL::kRow;
     float v[N];
-    row_to_chunk<N>(v, row);
     if (PREC == kPrecDF) {
-        // the whole cascade with double-float samples (the input is FP32:
-        // its low parts start at zero); the output is rounded once
-        float vl[N];
-#pragma unroll
-        for (int m = 0; m < N; ++m) vl[m] = 0.f;
-#pragma unroll 1
-        for (int k = 0; k < K; ++k) {
-            const Coef32* cf = cf0 + k;
-            const SecDF sd = load_secdf(cf);
-            const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane];
-            float* zf_dst = ZF ? p.zf + ((int64_t)sg.c * p.kmax + k) * 2 : nullptr;
-            const float4 zz = zs[k];
-            df z1{zz.x, zz.y}, z2{zz.z, zz.w};
-            pipe_section_dfx<N, ZF>(v, vl, sd, cf->phi_pow, cf->phi_lo, lp, lpl, z1, z2,
-                                    lane == owner, mq, zf_dst);
-            if (lane == 0) zs[k] = make_float4(z1.hi, z1.lo, z2.hi, z2.lo);
-        }
-#pragma unroll
-        for (int m = 0; m < N; ++m) v[m] = v[m] + vl[m];
+        dfx_group<N, ZF>(p, cf0, K, sg.c, row, zs, lane, owner, mq);
+        row_to_chunk<N>(v, row);
     } else {
+    row_to_chunk<N>(v, row);
     // one copy of the section code (a rolled loop keeps the kernel's
     // instruction footprint inside the instruction cache); plain (L1-cached)
     // loads at the point of use: read-only loads would be hoisted out of the
