@@ -423,10 +423,37 @@ def lowpass_leg(P, dev, steps: int = 50):
         g.replay()
     torch.cuda.synchronize()
     ms = replay_ms(g, steps)
-    return {"workload": wl.name, "samples": wl.total, "latency_us": ms * 1e3,
-            "value": wl.total / (ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-            "step": "sos_filter (prepare + apply), one CUDA-graph replay"}, \
-        [ParityJob("lowpass", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), None, y, 1e-5)]
+    # the streaming mode: the same 8,192 samples as one block of a stream
+    # (one launch, tables prepared once), timed per launch
+    st = P.SosStream(wl.sos, wl.total)
+    ys = torch.empty_like(wl.x)
+    x2 = wl.x.view(1, -1)
+    gs = graph_of(lambda: st(x2, ys.view(1, -1)))
+    ms_s = replay_ms(gs, steps)
+    st.reset()
+    st(x2, ys.view(1, -1))  # one block from zero state, for the parity check
+    # audio-like: 64 channels of the 16th-order band-pass, 256-sample blocks
+    bp = workloads.plain_bandpass16(n=16)
+    sos64 = bp.sos.to(dev).expand(64, -1, -1).contiguous()
+    st64 = P.SosStream(sos64, 256)
+    xb = torch.randn(64, 256, device=dev)
+    yb = torch.empty_like(xb)
+    gb = graph_of(lambda: st64(xb, yb))
+    ms_b = replay_ms(gb, steps)
+    return {"workload": wl.name, "samples": wl.total, "latency_us": ms_s * 1e3,
+            "value": wl.total / (ms_s * 1e-3) / 1e9, "unit": "Gsamples/s",
+            "step": "sos_stream: the signal as one block of a stream (one launch, one warp, "
+                    "tables prepared once), one CUDA-graph replay",
+            "latency_us_sos_filter": ms * 1e3,
+            "sos_filter_step": "sos_filter (prepare + apply), one CUDA-graph replay",
+            "stream_64ch_bp16_256": {"latency_us": ms_b * 1e3,
+                                     "value": 64 * 256 / (ms_b * 1e-3) / 1e9,
+                                     "unit": "Gsamples/s",
+                                     "step": "sos_stream, 64 channels x 256-sample blocks of the "
+                                             "16th-order band-pass, one launch per block"}}, \
+        [ParityJob("lowpass", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), None, y, 1e-5),
+         ParityJob("lowpass_stream", wl.x, wl.sos.cpu(), wl.K.cpu(), wl.lengths.numpy(), None,
+                   ys, 1e-5)]
 
 
 def batched_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):

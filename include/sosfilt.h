@@ -217,6 +217,46 @@ sos_status sos_apply_carried(const float *x, int32_t n_channels, int32_t kmax,
                              void *workspace, size_t ws_bytes, const sos_tuning *tuning,
                              void *stream);
 
+/* Low-latency streaming: filters one block of `chunk` new samples of every
+ * channel, carrying each channel's state from the previous block, in one
+ * kernel launch (one warp per channel, no plan launch, no waits between
+ * warps).  The paper's real-time scenario: a signal that arrives in blocks,
+ * the state handed from block to block exactly as between groups (Sec. V),
+ * the transposed-direct-form-II state of Eq. feedforward_block_uniform's
+ * corrections.
+ *   x, y      device FP32 [n_channels][chunk], channel-major (y must not
+ *             overlap x)
+ *   state     device FP32 [n_channels][kmax][2], in/out: the state before
+ *             this block on entry (zeros for a fresh stream), after it on
+ *             return; rows k >= K[c] are left as they are
+ *   workspace a workspace on which sos_prepare has run with the channels'
+ *             sos and K, lengths all equal to `chunk`, and the same tuning
+ *             (the coefficient tables are reused by every block; prepare
+ *             again when the coefficients change)
+ * Channels with K[c] = 0 copy x to y.  Precision classes (sos_plan_extended)
+ * apply as in sos_filter.  Asynchronous on `stream`; argument errors are
+ * returned at once.  Consecutive blocks of a stream must be ordered on the
+ * GPU (same stream, or events). */
+sos_status sos_stream(const float *x, float *y, float *state, int32_t n_channels, int32_t kmax,
+                      int64_t chunk, void *workspace, size_t ws_bytes, const sos_tuning *tuning,
+                      void *stream);
+
+/* Zero-phase (forward-backward) filtering: y = R H R H x, H the cascade
+ * from zero state and R time reversal within each channel, so that the
+ * overall response is |H(e^jw)|^2 with no phase shift (the cascade applied
+ * to the signal and again to its time reversal).  No edge padding and no
+ * initial-condition matching: the plain composition (callers that want
+ * scipy's odd-extension padding pad x themselves).  Arguments as in
+ * sos_filter, plus tmp: device FP32 [sum len], caller-owned scratch for the
+ * intermediate signal (none of x, y, tmp may overlap).  Five launches on
+ * `stream` (plan, forward pass, reversal, forward pass, reversal).  No
+ * counterpart in the paper: a use of the paper's filter, the cascade run
+ * twice. */
+sos_status sos_filtfilt(const float *x, const double *sos, const int32_t *K, int32_t n_channels,
+                        int32_t kmax, const int64_t *lengths, const int64_t *lengths_host, float *y,
+                        float *tmp, void *workspace, size_t ws_bytes, const sos_tuning *tuning,
+                        void *stream);
+
 /* sos_filter without a caller-allocated workspace (the paper has no
  * counterpart; this is a deployment convenience).  Some callers cannot call
  * cudaMalloc at all: real-time audio or control callbacks where its latency

@@ -165,6 +165,28 @@ def sosfilt(x, sos, K=None, lengths=None, zi=None):
     return default().sosfilt(x, sos, K, lengths, zi)
 
 
+def sosfiltfilt(x, sos, K=None, lengths=None):
+    """Zero-phase forward-backward filtering, written out as its definition:
+    the cascade from zero state over each channel, the result reversed in
+    time, the cascade again, reversed back (y = R H R H x).  FP64."""
+    x = np.asarray(x, dtype=np.float64)
+    sos = np.asarray(sos, dtype=np.float64)
+    if sos.ndim == 2:
+        sos = sos[None]
+    C = sos.shape[0]
+    lengths = np.array([x.size]) if lengths is None else np.asarray(lengths, dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(lengths)])
+
+    def rev(v):
+        out = np.empty_like(v)
+        for c in range(C):
+            out[off[c]:off[c + 1]] = v[off[c]:off[c + 1]][::-1]
+        return out
+    y1, _ = sosfilt(x, sos, K=K, lengths=lengths)
+    y2, _ = sosfilt(rev(y1), sos, K=K, lengths=lengths)
+    return rev(y2)
+
+
 def sosfilt_adjoint(x, sos, g_y, K=None, lengths=None, zi=None, g_zf=None):
     """See :meth:`Oracle.sosfilt_adjoint`."""
     return default().sosfilt_adjoint(x, sos, g_y, K, lengths, zi, g_zf)

@@ -21,8 +21,8 @@ import torch
 from . import _abi
 from ._abi import SosError, sos_tuning  # noqa: F401
 
-__all__ = ["SosFilter", "sosfilt", "sosfilt_diff", "SosFilterFunction", "SosError", "sos_tuning",
-           "build"]
+__all__ = ["SosFilter", "SosStream", "sosfilt", "sosfiltfilt", "sosfilt_diff", "SosFilterFunction", "SosError",
+           "sos_tuning", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -191,6 +191,27 @@ class SosFilter:
             raise SosError(st, "sos_plan_extended")
         return e
 
+    def filtfilt(self, x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                 y: Optional[torch.Tensor] = None, tmp: Optional[torch.Tensor] = None):
+        """Zero-phase filtering, y = R H R H x (sos_filtfilt)."""
+        C, kmax = self.n_channels, self.kmax
+        _check_device(x, "x")
+        if x.dtype != torch.float32 or not x.is_contiguous() or x.numel() != self.total:
+            raise ValueError("x must be contiguous float32 with sum(lengths) elements")
+        sos = sos.reshape(C, kmax, 6).contiguous()
+        if K is None:
+            K = torch.full((C,), kmax, dtype=torch.int32, device=x.device)
+        y = torch.empty_like(x) if y is None else y
+        tmp = torch.empty_like(x) if tmp is None else tmp
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_filtfilt(x.data_ptr(), sos.data_ptr(), K.data_ptr(), C, kmax,
+                               self.lengths.data_ptr(), self.lengths_host.data_ptr(), y.data_ptr(),
+                               tmp.data_ptr(), self.workspace.data_ptr(), self.ws_bytes, self.tuning,
+                               stream)
+        if st != 0:
+            raise SosError(st, "sos_filtfilt")
+        return y
+
     def plan_recomputed(self) -> int:
         """Channels whose tables the latest prepare() recomputed (0: all came
         from the plan cache); synchronises the current stream."""
@@ -218,6 +239,61 @@ class SosFilter:
         of the latest call (0 = OK)."""
         stream = torch.cuda.current_stream(self.device).cuda_stream
         return _abi.sos_device_status(self.workspace.data_ptr(), stream)
+
+
+class SosStream:
+    """Block-by-block filtering of C channels (the low-latency streaming
+    mode): each call filters the next ``chunk`` samples of every channel in
+    one kernel launch, carrying the state on the device from call to call.
+
+        st = SosStream(sos, chunk)                 # sos [C, K, 6] float64, CUDA
+        for block in blocks:                       # block: [C, chunk] float32
+            y = st(block)
+    """
+
+    def __init__(self, sos: torch.Tensor, chunk: int, K: Optional[torch.Tensor] = None,
+                 zi: Optional[torch.Tensor] = None, tuning: Optional[Sequence[int]] = None):
+        _check_device(sos, "sos")
+        sos = sos if sos.dim() == 3 else sos.unsqueeze(0)
+        self.n_channels, self.kmax = int(sos.shape[0]), int(sos.shape[1])
+        self.chunk = int(chunk)
+        if self.chunk < 1:
+            raise ValueError("chunk must be positive")
+        if tuning is None:
+            # latency: the smallest group that holds a chunk, N in {16, 32, 64}
+            n = 16 if self.chunk <= 512 else 32
+            tuning = (n, 8, 1, 0)
+        self.plan = SosFilter([self.chunk] * self.n_channels, self.kmax, tuning=tuning,
+                              device=sos.device)
+        self.sos = sos.contiguous()
+        self.K = (K if K is not None else
+                  torch.full((self.n_channels,), self.kmax, dtype=torch.int32, device=sos.device))
+        self.plan.prepare(self.sos, self.K)
+        self.state = torch.zeros((self.n_channels, self.kmax, 2), dtype=torch.float32,
+                                 device=sos.device)
+        if zi is not None:
+            self.state.copy_(zi.reshape(self.n_channels, self.kmax, 2))
+
+    def __call__(self, x: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
+        _check_device(x, "x")
+        if x.dtype != torch.float32 or not x.is_contiguous() or \
+                x.numel() != self.n_channels * self.chunk:
+            raise ValueError("x must be contiguous float32 [C, chunk]")
+        if y is None:
+            y = torch.empty_like(x)
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_stream(x.data_ptr(), y.data_ptr(), self.state.data_ptr(), self.n_channels,
+                             self.kmax, self.chunk, self.plan.workspace.data_ptr(),
+                             self.plan.ws_bytes, self.plan.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_stream")
+        return y
+
+    def reset(self, zi: Optional[torch.Tensor] = None) -> None:
+        if zi is None:
+            self.state.zero_()
+        else:
+            self.state.copy_(zi.reshape(self.n_channels, self.kmax, 2))
 
 
 _plans = {}
@@ -281,6 +357,29 @@ class SosFilterFunction(torch.autograd.Function):
                                           want_zi=ctx.has_zi)
         return gx, gsos.reshape(sos.shape), (gzi.reshape(zi.shape) if ctx.has_zi else None), \
             None, None
+
+
+def sosfiltfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                lengths=None, tuning=None) -> torch.Tensor:
+    """Zero-phase forward-backward filtering of x (float32, CUDA, packed
+    channels): the cascade applied forward, then to the time-reversed result,
+    reversed back (no edge padding)."""
+    _check_device(x, "x")
+    sos3 = sos if sos.dim() == 3 else sos.unsqueeze(0)
+    C, kmax = int(sos3.shape[0]), int(sos3.shape[1])
+    if lengths is None:
+        if C != 1:
+            raise ValueError("lengths are required for more than one channel")
+        lengths = [x.numel()]
+    lh = tuple(int(v) for v in torch.as_tensor(lengths).reshape(-1).tolist())
+    key = (x.device, lh, kmax, tuple(tuning) if tuning is not None else None)
+    plan = _plans.get(key)
+    if plan is None:
+        plan = SosFilter(lh, kmax, tuning=tuning, device=x.device)
+        if len(_plans) > 16:
+            _plans.clear()
+        _plans[key] = plan
+    return plan.filtfilt(x.contiguous(), sos3.contiguous(), K)
 
 
 def sosfilt_diff(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,

@@ -88,6 +88,10 @@ def load(build_if_missing: bool = False):
         lib.sos_filter_static.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, tp, vp,
                                           ctypes.POINTER(ctypes.c_int32)]
         lib.sos_filter_static.restype = ctypes.c_int
+        lib.sos_filtfilt.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
+        lib.sos_filtfilt.restype = ctypes.c_int
+        lib.sos_stream.argtypes = [vp, vp, vp, i32, i32, i64, vp, sz, tp, vp]
+        lib.sos_stream.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
         lib.sos_backward_workspace_size.argtypes = [i32, i32, vp, tp]
@@ -166,6 +170,22 @@ def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y,
                                       _tuning(tuning), V(stream),
                                       ctypes.byref(ds) if want_status else None))
     return st, (int(ds.value) if want_status else None)
+
+
+def sos_filtfilt(x, sos, K, n_channels, kmax, lengths, lengths_host, y, tmp, ws, ws_bytes, tuning,
+                 stream) -> int:
+    """All pointer arguments are integers."""
+    V = ctypes.c_void_p
+    return int(load().sos_filtfilt(V(x), V(sos), V(K), n_channels, kmax, V(lengths),
+                                   V(lengths_host), V(y), V(tmp), V(ws), ws_bytes, _tuning(tuning),
+                                   V(stream)))
+
+
+def sos_stream(x, y, state, n_channels, kmax, chunk, ws, ws_bytes, tuning, stream) -> int:
+    """All pointer arguments are integers."""
+    V = ctypes.c_void_p
+    return int(load().sos_stream(V(x), V(y), V(state), n_channels, kmax, int(chunk), V(ws),
+                                 ws_bytes, _tuning(tuning), V(stream)))
 
 
 def sos_device_status(ws_ptr: int, stream: int) -> int:

@@ -1,6 +1,7 @@
 // C ABI of the library (declared in include/sosfilt.h): argument checks,
 // workspace carving and the two launches of one call (plan, forward).
 #include <cstring>
+#include <vector>
 
 #include "sos_common.cuh"
 
@@ -13,6 +14,9 @@ bool pipe_supported(int N);
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early);
 int warpseg_ctas_per_sm(int N, int algo);
 int warpseg_warps_per_cta();
+cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream);
+cudaError_t launch_reverse(const float* src, float* dst, const Params& p, int64_t max_len,
+                           cudaStream_t stream);
 }  // namespace sosf
 
 using namespace sosf;
@@ -304,6 +308,73 @@ sos_status sos_filter(const float* x, const double* sos, const int32_t* K, int32
     if (s != SOS_OK) return s;
     return sos_apply(x, n_channels, kmax, lengths_host, zi, y, zf, workspace, ws_bytes, tuning,
                      stream);
+}
+
+sos_status sos_stream(const float* x, float* y, float* state, int32_t n_channels, int32_t kmax,
+                      int64_t chunk, void* workspace, size_t ws_bytes, const sos_tuning* tuning,
+                      void* stream) {
+    if (chunk < 0 || n_channels < 1) return SOS_ERR_ARG;
+    if (chunk > 0 && (!x || !y)) return SOS_ERR_ARG;
+    // the workspace was carved by sos_prepare for n_channels channels of
+    // `chunk` samples each: carve it the same way
+    std::vector<int64_t> lh((size_t)n_channels, chunk);
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    const sos_status s = setup(n_channels, kmax, lh.data(), workspace, ws_bytes, tuning, &p,
+                               &tiles, &total);
+    if (s != SOS_OK) return s;
+    if (x && y && total > 0) {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t bytes = sizeof(float) * (size_t)total;
+        if (xb < yb + bytes && yb < xb + bytes) return SOS_ERR_ARG;
+    }
+    p.x = x;
+    p.y = y;
+    p.zi = state;
+    p.zf = state;
+    if (chunk == 0) return SOS_OK;
+    if (launch_stream(p, chunk, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
+sos_status sos_filtfilt(const float* x, const double* sos, const int32_t* K, int32_t n_channels,
+                        int32_t kmax, const int64_t* lengths, const int64_t* lengths_host, float* y,
+                        float* tmp, void* workspace, size_t ws_bytes, const sos_tuning* tuning,
+                        void* stream) {
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p, &tiles,
+                         &total);
+    if (s != SOS_OK) return s;
+    if (!sos || !K || !lengths) return SOS_ERR_ARG;
+    if (total > 0 && (!x || !y || !tmp)) return SOS_ERR_ARG;
+    if (total > 0) {
+        const size_t bytes = sizeof(float) * (size_t)total;
+        const char* b[3] = {reinterpret_cast<const char*>(x), reinterpret_cast<const char*>(y),
+                            reinterpret_cast<const char*>(tmp)};
+        for (int i = 0; i < 3; ++i)
+            for (int j = i + 1; j < 3; ++j)
+                if (b[i] < b[j] + bytes && b[j] < b[i] + bytes) return SOS_ERR_ARG;
+    }
+    int64_t max_len = 0;
+    for (int32_t c = 0; c < n_channels; ++c) max_len = lengths_host[c] > max_len ? lengths_host[c] : max_len;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // forward pass (zero state), reversal, forward pass of the reversed
+    // signal, reversal: y = R H R H x
+    s = sos_prepare(sos, K, n_channels, kmax, lengths, lengths_host, workspace, ws_bytes, tuning,
+                    stream);
+    if (s != SOS_OK) return s;
+    s = sos_apply(x, n_channels, kmax, lengths_host, nullptr, tmp, nullptr, workspace, ws_bytes,
+                  tuning, stream);
+    if (s != SOS_OK) return s;
+    if (launch_reverse(tmp, y, p, max_len, st) != cudaSuccess) return SOS_ERR_CUDA;
+    s = sos_apply(y, n_channels, kmax, lengths_host, nullptr, tmp, nullptr, workspace, ws_bytes,
+                  tuning, stream);
+    if (s != SOS_OK) return s;
+    if (launch_reverse(tmp, y, p, max_len, st) != cudaSuccess) return SOS_ERR_CUDA;
+    return SOS_OK;
 }
 
 sos_status sos_device_status(void* workspace, void* stream) {

@@ -271,6 +271,54 @@ __device__ __forceinline__ void ws_segment(const Params& p, const SegGeom& sg, f
     }
 }
 
+// One segment of a channel within its memory horizon, in the instantiation
+// its channel needs (identity, cyclic reduction, FP32 PH, per-section
+// extended precision, or double-float samples).
+template <int N, bool CRK>
+__device__ __forceinline__ void ws_run_segment(const Params& p, const SegGeom& sg, float* slots,
+                                               float4* zs, int lane, int& cur, bool& pending,
+                                               const float* nsrc, int64_t nrem) {
+    if (sg.K == 0) {
+        // identity channel: copy the segment's own samples
+        for (int64_t i = sg.out_lo + lane; i < sg.out_hi; i += 32)
+            p.y[sg.off + i] = __ldg(p.x + sg.off + i);
+    } else {
+        const ChanInfo& ci = p.chan[sg.c];
+        const bool fact = ci.mode != 0;
+        // the channel's precision class (sos_plan_extended): 3 = the whole
+        // cascade in double-float, 1..2 = some sections in extended
+        // precision, 0 = FP32
+        const int ext = ci.ext;
+        // cyclic reduction when the call asks for it and every section of
+        // the channel is well conditioned for it (FP32 channels only), PH
+        // otherwise
+        bool cr = CRK && ext == 0;
+        for (int k = 0; k < sg.K && cr; ++k)
+            cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
+        if (ext >= 3)
+            ws_segment<N, false, false, kPrecDF>(p, sg, slots, zs, lane, cur, pending,
+                                                 nsrc, nrem);
+        else if (CRK && fact && cr)
+            ws_segment<N, true, CRK, kPrecF32>(p, sg, slots, zs, lane, cur, pending,
+                                               nsrc, nrem);
+        else if (CRK && cr)
+            ws_segment<N, false, CRK, kPrecF32>(p, sg, slots, zs, lane, cur, pending,
+                                                nsrc, nrem);
+        else if (fact && ext)
+            ws_segment<N, true, false, kPrecSect>(p, sg, slots, zs, lane, cur, pending,
+                                                  nsrc, nrem);
+        else if (fact)
+            ws_segment<N, true, false, kPrecF32>(p, sg, slots, zs, lane, cur, pending,
+                                                 nsrc, nrem);
+        else if (ext)
+            ws_segment<N, false, false, kPrecSect>(p, sg, slots, zs, lane, cur, pending,
+                                                   nsrc, nrem);
+        else
+            ws_segment<N, false, false, kPrecF32>(p, sg, slots, zs, lane, cur, pending,
+                                                  nsrc, nrem);
+    }
+}
+
 // CRK: the cyclic-reduction instantiation (algo 2).  The PH one carries no
 // cyclic-reduction code, so its register allocation does not pay for it.
 template <int N, bool CRK>
@@ -310,45 +358,7 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
                 nrem = nx.len - nx.cstart;
             }
         }
-        if (sg.K == 0) {
-            // identity channel: copy the segment's own samples
-            for (int64_t i = sg.out_lo + lane; i < sg.out_hi; i += 32)
-                p.y[sg.off + i] = __ldg(p.x + sg.off + i);
-        } else {
-            const ChanInfo& ci = p.chan[sg.c];
-            const bool fact = ci.mode != 0;
-            // the channel's precision class (sos_plan_extended): 3 = the whole
-            // cascade in double-float, 1..2 = some sections in extended
-            // precision, 0 = FP32
-            const int ext = ci.ext;
-            // cyclic reduction when the call asks for it and every section of
-            // the channel is well conditioned for it (FP32 channels only), PH
-            // otherwise
-            bool cr = CRK && ext == 0;
-            for (int k = 0; k < sg.K && cr; ++k)
-                cr = __ldg(&p.c32[(int64_t)sg.c * p.kmax + k].cr_misc.w) != 0.f;
-            if (ext >= 3)
-                ws_segment<N, false, false, kPrecDF>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                     nsrc, nrem);
-            else if (CRK && fact && cr)
-                ws_segment<N, true, CRK, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                   nsrc, nrem);
-            else if (CRK && cr)
-                ws_segment<N, false, CRK, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                    nsrc, nrem);
-            else if (fact && ext)
-                ws_segment<N, true, false, kPrecSect>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                      nsrc, nrem);
-            else if (fact)
-                ws_segment<N, true, false, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                     nsrc, nrem);
-            else if (ext)
-                ws_segment<N, false, false, kPrecSect>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                       nsrc, nrem);
-            else
-                ws_segment<N, false, false, kPrecF32>(p, sg, slots, s_z[w], lane, cur, pending,
-                                                      nsrc, nrem);
-        }
+        ws_run_segment<N, CRK>(p, sg, slots, s_z[w], lane, cur, pending, nsrc, nrem);
         d = dn;
         if (d < total) sg = seg_geom<WC::kGroup>(p, d);
     }
@@ -364,6 +374,41 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
             __threadfence();
         }
     }
+}
+
+// Low-latency streaming: one warp per channel filters the channel's whole
+// chunk (x, y: [C][chunk]) through all K sections, group after group, from
+// the state `p.zi` and leaves the final state in `p.zf` (the same array for
+// in-place state: each warp reads its channel's state before it writes it).
+// No plan launch, no segment hand-out, no waits on other warps: one launch
+// per call, with the coefficient tables of an earlier sos_prepare.  The
+// paper's real-time scenario (a signal arriving in blocks, the state carried
+// from one block to the next, Sec. V's group chaining across calls).
+template <int N>
+__global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>())
+    sos_stream_kernel(Params p, int64_t chunk) {
+    using WC = WsCfg<N>;
+    extern __shared__ float4 s_ws4[];
+    __shared__ float4 s_z[kWsWarps][kMaxSections];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int c = (int)blockIdx.x * kWsWarps + w;
+    if (c >= p.C || chunk <= 0) return;
+    float* slots = reinterpret_cast<float*>(s_ws4) + (size_t)w * 2 * WC::kSlot;
+    SegGeom sg;
+    sg.c = c;
+    sg.si = 0;
+    sg.off = (int64_t)c * chunk;
+    sg.len = chunk;
+    sg.out_lo = 0;
+    sg.out_hi = chunk;
+    sg.cstart = 0;
+    sg.ngroups = (int)((chunk + WC::kGroup - 1) / WC::kGroup);
+    sg.horizon = 0;
+    sg.K = p.chan[c].K;
+    int cur = 0;
+    bool pending = false;
+    ws_run_segment<N, false>(p, sg, slots, s_z[w], lane, cur, pending, nullptr, 0);
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 #define SOSF_WS(N_, CR_) reinterpret_cast<const void*>(&sos_warpseg_kernel<N_, CR_>)
@@ -396,6 +441,23 @@ int warpseg_ctas_per_sm(int N, int algo) {
 }
 
 int warpseg_warps_per_cta() { return kWsWarps; }
+
+cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream) {
+    const void* fn = p.N == 16 ? reinterpret_cast<const void*>(&sos_stream_kernel<16>)
+                   : p.N == 32 ? reinterpret_cast<const void*>(&sos_stream_kernel<32>)
+                               : reinterpret_cast<const void*>(&sos_stream_kernel<64>);
+    static bool attr[3] = {false, false, false};
+    const int idx = p.N == 16 ? 0 : p.N == 32 ? 1 : 2;
+    if (!attr[idx]) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(p.N));
+        if (e != cudaSuccess) return e;
+        attr[idx] = true;
+    }
+    void* args[] = {const_cast<Params*>(&p), &chunk};
+    const unsigned grid = (unsigned)((p.C + kWsWarps - 1) / kWsWarps);
+    return cudaLaunchKernel(fn, dim3(grid), dim3(kWsThreads), args, ws_smem(p.N), stream);
+}
 
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early) {
     if (warpseg_ctas_per_sm(p.N, p.algo) < 1) return cudaErrorInvalidConfiguration;

@@ -379,7 +379,38 @@ def pin_adjoint(orc):
                 assert abs(fd - gs[0, k, j]) <= 1e-6 * (1 + abs(fd)), (T, k, j, fd, gs[0, k, j])
 
 
+def pin_filtfilt_autocorrelation_and_zero_phase(orc=None):
+    """Zero-phase filtering (oracle.sosfiltfilt, y = R H R H x): of a unit
+    impulse at sample c of a zero signal it gives the autocorrelation of the
+    cascade's impulse response, y[c + n] = sum_k h[k] h[k + |n|] (symmetric
+    about c), with h the convolution of the closed-form section responses;
+    and a cosine far from the ends comes out scaled by |H(e^jw)|^2 with no
+    phase shift (H evaluated from the coefficients)."""
+    import oracle
+    rs = np.random.RandomState(17)
+    sos = random_stable_sos(rs, 3, rmax=0.8)
+    n = 4096
+    h = section_impulse(sos[0], n)
+    for row in sos[1:]:
+        h = np.convolve(h, section_impulse(row, n))[:n]
+    c = 2000
+    x = np.zeros(n)
+    x[c] = 1.0
+    y = oracle.sosfiltfilt(x, sos)
+    acf = np.array([np.dot(h[:n - m], h[m:]) for m in range(600)])
+    for m in range(600):
+        assert abs(y[c + m] - acf[m]) <= 1e-12 * acf[0]
+        assert abs(y[c - m] - acf[m]) <= 1e-12 * acf[0]
+    w = 0.3
+    t = np.arange(20000, dtype=np.float64)
+    yc = oracle.sosfiltfilt(np.cos(w * t), sos)
+    g = abs(rational_response(sos, np.array([w]))[0]) ** 2
+    mid = slice(8000, 12000)
+    assert np.max(np.abs(yc[mid] - g * np.cos(w * t[mid]))) <= 1e-9 * max(g, 1.0)
+
+
 ALL_PINS = [
+    pin_filtfilt_autocorrelation_and_zero_phase,
     pin_single_biquad_impulse,
     pin_cascade_is_convolution,
     pin_frequency_response,

@@ -1,0 +1,91 @@
+"""The low-latency streaming mode (sos_stream): a signal filtered block by
+block, one launch per block, the state carried on the device, must equal the
+one-shot result of the oracle (the final state too), whatever the block
+length, including blocks shorter than a group, ragged against it, and single
+samples."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import rng, workloads
+from test_gpu_forward import _lib, check, random_case
+
+pytestmark = pytest.mark.gpu
+
+
+def _stream(P, x2d, sos, K, zi, chunk, tuning=None):
+    C, T = x2d.shape
+    st = P.SosStream(sos.cuda(), chunk, K=K.cuda(), zi=zi.cuda() if zi is not None else None,
+                     tuning=tuning)
+    out = torch.empty_like(x2d)
+    nblk = T // chunk
+    for b in range(nblk):
+        blk = x2d[:, b * chunk:(b + 1) * chunk].contiguous()
+        out[:, b * chunk:(b + 1) * chunk] = st(blk)
+    assert st.plan.device_status() == 0
+    return out, st.state
+
+
+@pytest.mark.parametrize("chunk,tuning", [(256, None), (1000, None), (4096, (32, 8, 1, 0)),
+                                          (3000, (64, 8, 1, 0))])
+def test_stream_blocks_match_one_shot(chunk, tuning):
+    P = _lib()
+    C, T = 6, 1 << 20
+    T = (T // chunk) * chunk
+    x, sos, K, L, zi = random_case(91, [T] * C, 8, rmax=0.97)
+    K[1] = 3
+    K[4] = 0
+    x2d = x.view(C, T).cuda()
+    y, state = _stream(P, x2d, sos, K, zi, chunk, tuning)
+    y_ref, zf_ref = oracle.sosfilt(x.double().numpy(), sos.numpy(), K=K.numpy(), lengths=L.numpy(),
+                                   zi=zi.double().numpy())
+    zf = state.cpu().numpy().copy()
+    for c in range(C):  # rows past K keep the caller's state; the oracle writes 0
+        zf[c, int(K[c]):] = 0.0
+    check(y.reshape(-1).cpu().numpy(), zf, y_ref, zf_ref, L.numpy(), K.numpy(), 1e-5)
+
+
+def test_stream_single_samples_and_short_blocks():
+    """Blocks of 1 and 7 samples (far below one group), alternating, on the
+    16th-order band-pass."""
+    P = _lib()
+    wl = workloads.plain_bandpass16(n=4096)
+    x = wl.x.cuda()
+    st = P.SosStream(wl.sos.cuda(), 1)
+    st7 = None
+    out = []
+    pos = 0
+    use_seven = False
+    while pos < 4096:
+        if use_seven and pos + 7 <= 4096:
+            if st7 is None:
+                st7 = P.SosStream(wl.sos.cuda(), 7)
+            st7.state.copy_(st.state)
+            out.append(st7(x[pos:pos + 7].contiguous().view(1, 7)).view(-1))
+            st.state.copy_(st7.state)
+            pos += 7
+        else:
+            out.append(st(x[pos:pos + 1].contiguous().view(1, 1)).view(-1))
+            pos += 1
+        use_seven = not use_seven
+    y = torch.cat(out)
+    ref, zf_ref = oracle.sosfilt(wl.x.double().numpy(), wl.sos.numpy())
+    err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err <= 1e-5, err
+    zf = st.state.cpu().double().numpy()
+    assert np.linalg.norm(zf - zf_ref) <= 1e-5 * np.linalg.norm(zf_ref)
+
+
+def test_stream_rejects_bad_arguments():
+    P = _lib()
+    wl = workloads.plain_lowpass(n=256)
+    st = P.SosStream(wl.sos.cuda(), 256)
+    with pytest.raises(ValueError):
+        st(torch.zeros(255, device="cuda"))
+    # overlapping x and y
+    buf = torch.zeros(512, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    r = P._abi.sos_stream(buf.data_ptr(), buf.data_ptr() + 4, st.state.data_ptr(), 1, 1, 256,
+                          st.plan.workspace.data_ptr(), st.plan.ws_bytes, st.plan.tuning, stream)
+    assert r == -1
