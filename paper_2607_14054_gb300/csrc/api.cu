@@ -164,6 +164,7 @@ sos_status setup(int32_t n_channels, int32_t kmax, const int64_t* lengths_host, 
     p->tb = reinterpret_cast<int64_t*>(ws + L.tb);
     p->tbp = reinterpret_cast<int64_t*>(ws + L.tbp);
     p->order = reinterpret_cast<int32_t*>(ws + L.order);
+    p->porder = reinterpret_cast<int32_t*>(ws + L.porder);
     p->rp = reinterpret_cast<int64_t*>(ws + L.rp);
     p->c32 = reinterpret_cast<Coef32*>(ws + L.c32);
     p->cdf = reinterpret_cast<CoefDF*>(ws + L.cdf);

@@ -929,61 +929,90 @@ __device__ __noinline__ void order_pass(const Params& p, unsigned long long* s_k
     const int lane = tid & 31, warp = tid >> 5;
     __shared__ int64_t s_carry;
     __shared__ int64_t s_wsum[32];
-    // ---- prefixes: look-back tiles of the carried channels (tb) and
-    // pipeline segments of the others (tbp) ----
+    // ---- prefixes: look-back tiles of the carried channels (tb, by
+    // channel) and segments of the channels within their horizon (tbp, by
+    // dispatch position: porder lists the channels run with double-float
+    // samples first, their segments costing about ten times the others',
+    // so that they are handed out first and do not trail the launch) ----
     __shared__ int64_t s_carry2;
     __shared__ int64_t s_wsum2[32];
+    // block-wide exclusive scan of one value per thread (every thread
+    // calls it); s_c carries the running total between rounds
+    auto scan = [&](int64_t v, int64_t* s_w, int64_t* s_c) -> int64_t {
+        int64_t inc = v;
+        for (int d = 1; d < 32; d <<= 1) {
+            const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += o;
+        }
+        if (lane == 31) s_w[warp] = inc;
+        __syncthreads();
+        int64_t wpre = 0;
+        for (int w = 0; w < warp; ++w) wpre += s_w[w];
+        const int64_t carry = *s_c;
+        __syncthreads();
+        if (tid == blockDim.x - 1) *s_c = carry + wpre + inc;
+        __syncthreads();
+        return carry + wpre + inc - v;
+    };
     if (tid == 0) {
         s_carry = 0;
         s_carry2 = 0;
     }
     __syncthreads();
     int carried = 0;
+    // channels run with double-float samples: tiles of carried channels, and
+    // the class-3 channels' dispatch positions
     for (int base = 0; base < C; base += blockDim.x) {
         const int c = base + tid;
-        int64_t nt = 0, ns = 0;
+        int64_t nt = 0, f3 = 0;
         if (c < C) {
             // written by other blocks of this launch: read past L1
             const int32_t hz = __ldcg(&p.chan[c].horizon), ntl = __ldcg(&p.chan[c].ntiles);
+            const int16_t ext = __ldcg(&p.chan[c].ext);
             if (hz < 0) {
                 nt = ntl;
                 if (nt > 1) carried = 1;
             } else {
-                ns = ntl;
+                f3 = ext >= 3 ? 1 : 0;
             }
         }
-        int64_t inc = nt, inc2 = ns;
-        for (int d = 1; d < 32; d <<= 1) {
-            const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-            const int64_t o2 = __shfl_up_sync(0xffffffffu, inc2, d);
-            if (lane >= d) {
-                inc += o;
-                inc2 += o2;
-            }
-        }
-        if (lane == 31) {
-            s_wsum[warp] = inc;
-            s_wsum2[warp] = inc2;
-        }
-        __syncthreads();
-        int64_t wpre = 0, wpre2 = 0;
-        for (int w = 0; w < warp; ++w) {
-            wpre += s_wsum[w];
-            wpre2 += s_wsum2[w];
-        }
-        const int64_t carry = s_carry, carry2 = s_carry2;
+        const int64_t t0 = scan(nt, s_wsum, &s_carry);
+        const int64_t q0 = scan(f3, s_wsum2, &s_carry2);
         if (c < C) {
-            p.tb[c] = carry + wpre + inc - nt;
-            p.tbp[c] = carry2 + wpre2 + inc2 - ns;
+            p.tb[c] = t0;
+            if (f3) p.porder[q0] = c;
         }
-        __syncthreads();
-        if (tid == blockDim.x - 1) {
-            s_carry = carry + wpre + inc;
-            s_carry2 = carry2 + wpre2 + inc2;
-        }
-        __syncthreads();
     }
-    const int64_t total = s_carry, total2 = s_carry2;
+    const int64_t total = s_carry, n3 = s_carry2;
+    __syncthreads();
+    if (tid == 0) s_carry2 = 0;
+    __syncthreads();
+    for (int base = 0; base < C; base += blockDim.x) {
+        const int c = base + tid;
+        int64_t f = 0;
+        if (c < C) {
+            const int32_t hz = __ldcg(&p.chan[c].horizon);
+            const int16_t ext = __ldcg(&p.chan[c].ext);
+            f = (hz >= 0 && ext >= 3) ? 0 : 1;
+        }
+        const int64_t q = scan(f, s_wsum2, &s_carry2);
+        if (c < C && f) p.porder[n3 + q] = c;
+    }
+    __syncthreads();  // porder complete (block-wide visibility of its global writes)
+    if (tid == 0) s_carry2 = 0;
+    __syncthreads();
+    for (int base = 0; base < C; base += blockDim.x) {
+        const int i = base + tid;
+        int64_t ns = 0;
+        if (i < C) {
+            const int c = p.porder[i];
+            const int32_t hz = __ldcg(&p.chan[c].horizon), ntl = __ldcg(&p.chan[c].ntiles);
+            if (hz >= 0) ns = ntl;
+        }
+        const int64_t q = scan(ns, s_wsum2, &s_carry2);
+        if (i < C) p.tbp[i] = q;
+    }
+    const int64_t total2 = s_carry2;
     const bool interleave = __syncthreads_or(carried) != 0 && C <= kMaxSortChannels;
     if (tid == 0) {
         const bool bad = __ldcg(&p.hdr->status) == SOS_ERR_WORKSPACE;

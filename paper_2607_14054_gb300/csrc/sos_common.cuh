@@ -189,7 +189,7 @@ struct __align__(16) CoefDF {
 constexpr int kWords = 6;  // inc z1.hi, z1.lo, z2.hi, z2.lo, agg z1, z2
 
 struct WsLayout {
-    size_t hdr, chan, tb, tbp, order, rp, c32, cdf, key, slots, total;
+    size_t hdr, chan, tb, tbp, order, porder, rp, c32, cdf, key, slots, total;
     int64_t cap_tiles;
 };
 
@@ -203,6 +203,7 @@ inline WsLayout ws_layout(int32_t C, int32_t kmax, int64_t cap_tiles) {
     L.tb = o;    o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
     L.tbp = o;   o = align_up(o + sizeof(int64_t) * ((size_t)C + 1), 256);
     L.order = o; o = align_up(o + sizeof(int32_t) * (size_t)C, 256);
+    L.porder = o; o = align_up(o + sizeof(int32_t) * (size_t)C, 256);
     // rounds of the interleaved dispatch: at most the longest channel's tile
     // count, which overlapping tiles (stride >= T / 2) at most double
     L.rp = o;    o = align_up(o + sizeof(int64_t) * (2 * (size_t)(cap_tiles > 0 ? cap_tiles : 0) + 2), 256);
@@ -228,7 +229,9 @@ struct Params {
     WsHeader* hdr;
     ChanInfo* chan;
     int64_t* tb;         // look-back tile prefix over the carried channels [C + 1]
-    int64_t* tbp;        // segment prefix over the pipelined channels [C + 1]
+    int64_t* tbp;        // segment prefix over the channels within their horizon, by
+                         // dispatch position [C + 1]
+    int32_t* porder;     // channel at each dispatch position of those segments [C]
     int32_t* order;      // channels by decreasing tile count (interleaved dispatch)
     int64_t* rp;         // tiles dispatched before round r [nrounds + 1]
     Coef32* c32;

@@ -28,14 +28,15 @@ struct SegGeom {
 
 template <int kGroup>
 __device__ __forceinline__ SegGeom seg_geom(const Params& p, int64_t d) {
-    int lo = 0, hi = p.C - 1;  // the largest c with tbp[c] <= d
+    int lo = 0, hi = p.C - 1;  // the largest position with tbp[pos] <= d
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (__ldg(&p.tbp[mid]) <= d) lo = mid; else hi = mid - 1;
     }
-    const ChanInfo ci = p.chan[lo];
+    const int c = __ldg(&p.porder[lo]);
+    const ChanInfo ci = p.chan[c];
     SegGeom g;
-    g.c = lo;
+    g.c = c;
     g.si = (int)(d - __ldg(&p.tbp[lo]));
     g.off = ci.off;
     g.len = ci.len;
