@@ -601,6 +601,56 @@ def backward_leg(P, dev, world, sms, sm_max, hbm_gbs, steps: int = 5):
                               "fma_per_sample_section": BWD_FMA_PER_SECTION}}
 
 
+def compare_leg(P, dev, sms, sm_max, hbm_gbs, steps: int = 5):
+    """The paper's algorithm comparison (Sec. VIII) on this GPU: the scalar
+    recursion, block filtering, PH and cyclic reduction on one 2^24-sample
+    channel of Butterworth band-pass cascades of K = 1, 2, 4, 8 sections, all
+    on the same segmentation by memory horizon; each algorithm at its best
+    segment length / tuning.  Gsamples/s and the fraction of the FP32
+    roofline (6K + 1 FMAs per sample against the FMA peak, or 8 bytes per
+    sample against HBM)."""
+    import torch
+    from synth import filters, rng
+    n = 1 << 24
+    x = rng.normal(2, rng.STREAM_SIGNAL, n, device=dev, dtype=torch.float32)
+    y = torch.empty_like(x)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    out = []
+    for K in (1, 2, 4, 8):
+        sos = torch.from_numpy(filters.butter_bandpass(K, 0.1, 0.2))[None].contiguous().to(dev)
+        Kt = torch.full((1,), K, dtype=torch.int32, device=dev)
+        roof = min(hbm_gbs * 1e9 / 8.0, sms * FP32_LANES_PER_SM * sm_max * 1e6 / (6 * K + 1)) / 1e9
+        row = {"K": K, "roofline_gsamples_per_s": roof}
+        for name, tunings in (("PH", [(16, 8, 1, 0), (32, 8, 1, 0), (32, 8, 1, 768),
+                                      (64, 8, 1, 0), (32, 8, 1, 4), (64, 8, 1, 4)]),
+                              ("CR", [(16, 8, 2, 0), (32, 8, 2, 0), (32, 8, 2, 768),
+                                      (64, 8, 2, 0), (32, 8, 2, 4), (64, 8, 2, 4)])):
+            best = None
+            for t in tunings:
+                plan = P.SosFilter([n], K, tuning=t, device=dev)
+                plan.prepare(sos, Kt)
+                g = graph_of(lambda: plan.apply(x, y))
+                ms = replay_ms(g, steps, flush)
+                if best is None or ms < best[0]:
+                    best = (ms, t)
+            row[name] = {"value": n / (best[0] * 1e-3) / 1e9, "tuning": list(best[1])}
+        plan = P.SosFilter([n], K, tuning=(32, 8, 1, 0), device=dev)
+        plan.prepare(sos, Kt)
+        for name in ("scalar", "block"):
+            best = None
+            for sl in (256, 1024, 4096, 16384, 65536):
+                g = graph_of(lambda: plan.apply_baseline(name, x, y, sl))
+                ms = replay_ms(g, steps, flush)
+                if best is None or ms < best[0]:
+                    best = (ms, sl)
+            row[name] = {"value": n / (best[0] * 1e-3) / 1e9, "seg_len": best[1]}
+        for name in ("scalar", "block", "PH", "CR"):
+            row[name]["frac_of_roofline"] = row[name]["value"] / roof
+        out.append(row)
+    return {"workload": "butter_bp(K)_0.1-0.2_1x16777216", "rows": out,
+            "note": "apply only (tables prepared once), L2 flushed between steps"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -614,7 +664,7 @@ def main():
     ap.add_argument("--clocks-out", default="")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the low-pass, batched, differentiation and stress legs")
-    ap.add_argument("--leg", default="", choices=["", "backward", "batched", "stress"],
+    ap.add_argument("--leg", default="", choices=["", "backward", "batched", "stress", "compare"],
                     help="run only this extra leg and print its figures (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -636,7 +686,8 @@ def main():
     if args.leg:
         fn = {"backward": lambda: backward_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps),
               "batched": lambda: batched_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps)[0],
-              "stress": lambda: stress_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps)[0]}
+              "stress": lambda: stress_leg(P, dev, world, sms, sm_max, hbm_gbs, args.steps)[0],
+              "compare": lambda: compare_leg(P, dev, sms, sm_max, hbm_gbs, args.steps)}
         line = {"leg": args.leg, **fn[args.leg]()}
         if rank == 0:
             print(json.dumps(line), flush=True)

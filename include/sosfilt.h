@@ -241,6 +241,30 @@ sos_status sos_stream(const float *x, float *y, float *state, int32_t n_channels
                       int64_t chunk, void *workspace, size_t ws_bytes, const sos_tuning *tuning,
                       void *stream);
 
+/* The comparison algorithms of the paper's evaluation (Sec. VIII, beside
+ * PH and cyclic reduction), on the same tables and the same parallel
+ * decomposition: each channel cut into segments of seg_len outputs (>= 32),
+ * every segment computed from its channel's memory horizon P earlier from
+ * zero state (the channel's zi for its first segment; a channel without a
+ * horizon is one segment), so that only the filtering of a segment differs.
+ *   algorithm 0: scalar -- one thread per segment runs each section's
+ *                recursion (Sec. II, Eq. complex_second_order) sample by
+ *                sample in FP32;
+ *   algorithm 1: block filtering (Sec. IV, Eq. block_filtering_equation) --
+ *                one warp per segment, blocks of L = 32 samples (one per
+ *                lane), each block and section as H x_n + H_b xbar_{n-1} -
+ *                H_a ybar_{n-1} with H the Toeplitz matrix of the section's
+ *                first 32 impulse-response samples: 32 + 4 block FMAs per
+ *                block.
+ * Arguments as in sos_apply (after sos_prepare on the same workspace, same
+ * tuning).  Every section runs in FP32 whatever its precision class.  For
+ * measurement against the method; not a faster path.  No counterpart
+ * beyond the algorithms themselves. */
+sos_status sos_apply_baseline(int32_t algorithm, const float *x, int32_t n_channels, int32_t kmax,
+                              const int64_t *lengths_host, const float *zi, float *y, float *zf,
+                              int64_t seg_len, void *workspace, size_t ws_bytes,
+                              const sos_tuning *tuning, void *stream);
+
 /* Zero-phase (forward-backward) filtering: y = R H R H x, H the cascade
  * from zero state and R time reversal within each channel, so that the
  * overall response is |H(e^jw)|^2 with no phase shift (the cascade applied

@@ -212,6 +212,22 @@ class SosFilter:
             raise SosError(st, "sos_filtfilt")
         return y
 
+    def apply_baseline(self, algorithm: str, x: torch.Tensor, y: torch.Tensor, seg_len: int,
+                       zi: Optional[torch.Tensor] = None, zf: Optional[torch.Tensor] = None):
+        """The comparison algorithms on this plan's tables: "scalar" or
+        "block" filtering (sos_apply_baseline), segments of seg_len."""
+        algo = {"scalar": 0, "block": 1}[algorithm]
+        stream = torch.cuda.current_stream(x.device).cuda_stream
+        st = _abi.sos_apply_baseline(algo, x.data_ptr(), self.n_channels, self.kmax,
+                                     self.lengths_host.data_ptr(),
+                                     zi.data_ptr() if zi is not None else 0, y.data_ptr(),
+                                     zf.data_ptr() if zf is not None else 0,
+                                     seg_len, self.workspace.data_ptr(), self.ws_bytes,
+                                     self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_apply_baseline")
+        return y, zf
+
     def plan_recomputed(self) -> int:
         """Channels whose tables the latest prepare() recomputed (0: all came
         from the plan cache); synchronises the current stream."""

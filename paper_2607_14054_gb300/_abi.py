@@ -88,6 +88,8 @@ def load(build_if_missing: bool = False):
         lib.sos_filter_static.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, tp, vp,
                                           ctypes.POINTER(ctypes.c_int32)]
         lib.sos_filter_static.restype = ctypes.c_int
+        lib.sos_apply_baseline.argtypes = [i32, vp, i32, i32, vp, vp, vp, vp, i64, vp, sz, tp, vp]
+        lib.sos_apply_baseline.restype = ctypes.c_int
         lib.sos_filtfilt.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
         lib.sos_filtfilt.restype = ctypes.c_int
         lib.sos_stream.argtypes = [vp, vp, vp, i32, i32, i64, vp, sz, tp, vp]
@@ -170,6 +172,15 @@ def sos_filter_static(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y,
                                       _tuning(tuning), V(stream),
                                       ctypes.byref(ds) if want_status else None))
     return st, (int(ds.value) if want_status else None)
+
+
+def sos_apply_baseline(algorithm, x, n_channels, kmax, lengths_host, zi, y, zf, seg_len, ws,
+                       ws_bytes, tuning, stream) -> int:
+    """algorithm 0 = scalar, 1 = block filtering; pointers as integers."""
+    V = ctypes.c_void_p
+    return int(load().sos_apply_baseline(int(algorithm), V(x), n_channels, kmax, V(lengths_host),
+                                         V(zi or None), V(y), V(zf or None), int(seg_len), V(ws),
+                                         ws_bytes, _tuning(tuning), V(stream)))
 
 
 def sos_filtfilt(x, sos, K, n_channels, kmax, lengths, lengths_host, y, tmp, ws, ws_bytes, tuning,

@@ -17,6 +17,8 @@ int warpseg_warps_per_cta();
 cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream);
 cudaError_t launch_reverse(const float* src, float* dst, const Params& p, int64_t max_len,
                            cudaStream_t stream);
+cudaError_t launch_compare(const Params& p, int algo, int64_t seg_len, int64_t max_segs,
+                           cudaStream_t stream);
 }  // namespace sosf
 
 using namespace sosf;
@@ -336,6 +338,41 @@ sos_status sos_stream(const float* x, float* y, float* state, int32_t n_channels
     p.zf = state;
     if (chunk == 0) return SOS_OK;
     if (launch_stream(p, chunk, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+        return SOS_ERR_CUDA;
+    return SOS_OK;
+}
+
+sos_status sos_apply_baseline(int32_t algorithm, const float* x, int32_t n_channels,
+                              int32_t kmax, const int64_t* lengths_host, const float* zi, float* y,
+                              float* zf, int64_t seg_len, void* workspace, size_t ws_bytes,
+                              const sos_tuning* tuning, void* stream) {
+    if (algorithm != 0 && algorithm != 1) return SOS_ERR_ARG;
+    if (seg_len < 32) return SOS_ERR_ARG;
+    Params p{};
+    int64_t tiles = 0, total = 0;
+    const sos_status s = setup(n_channels, kmax, lengths_host, workspace, ws_bytes, tuning, &p,
+                               &tiles, &total);
+    if (s != SOS_OK) return s;
+    if (total > 0 && (!x || !y)) return SOS_ERR_ARG;
+    if (x && y && total > 0) {
+        const char* xb = reinterpret_cast<const char*>(x);
+        const char* yb = reinterpret_cast<const char*>(y);
+        const size_t bytes = sizeof(float) * (size_t)total;
+        if (xb < yb + bytes && yb < xb + bytes) return SOS_ERR_ARG;
+    }
+    // segments per channel: at most ceil(len / seg_len) (channels without a
+    // horizon are one segment)
+    int64_t max_segs = 1;
+    for (int32_t c = 0; c < n_channels; ++c) {
+        const int64_t ns = (lengths_host[c] + seg_len - 1) / seg_len;
+        if (ns > max_segs) max_segs = ns;
+    }
+    p.x = x;
+    p.y = y;
+    p.zi = zi;
+    p.zf = zf;
+    if (launch_compare(p, algorithm, seg_len, max_segs, static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess)
         return SOS_ERR_CUDA;
     return SOS_OK;
 }
