@@ -39,13 +39,14 @@ __device__ __forceinline__ bool cmp_seg(const Params& p, int c, int64_t s, int64
     g.K = ci.K;
     g.out_lo = s * sl;
     g.out_hi = g.out_lo + sl < L ? g.out_lo + sl : L;
-    // warm-up from zero state P samples early; a segment whose warm-up would
-    // start within the plan's first segment of the channel (which the plan
-    // made long enough for the initial state's response to die out) starts
-    // at the channel's start from zi instead
+    // warm-up from zero state P samples early; with an initial state, a
+    // segment whose warm-up would start within the plan's first segment of
+    // the channel (which the plan made long enough for the initial state's
+    // response to die out) starts at the channel's start from zi instead
     g.cstart = s == 0 ? 0 : g.out_lo - P;
     g.first = s == 0;
-    if (g.cstart < ci.seg) {
+    if (g.cstart < 0) g.cstart = 0;
+    if (p.zi && s > 0 && g.cstart < ci.seg) {
         g.cstart = 0;
         g.first = true;
     }
