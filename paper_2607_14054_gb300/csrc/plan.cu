@@ -321,8 +321,18 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
 // products.  Numerators enter scaled by 1 / max |b_j| (the scales cancel in
 // the ratio).  Returns the estimate, or -1 where it cannot be formed (a pole
 // at zero or coincident poles, a sum that cancels, overflow).
+// Shared-memory scratch of the precision warp (its loops stay rolled: the
+// code runs once per plan, and straight-line code of that size would be
+// fetched from instruction memory one miss at a time).
+struct HandoffScratch {
+    cpx W[2 * kMaxSections][2 * kMaxSections];  // q_ij / (1 - q_ij)
+    cpx F[2 * kMaxSections][kMaxSections];      // F_i(m)
+    cpx R[2 * kMaxSections];                    // residues of the current cascade
+    float E[2 * kMaxSections];                  // prefix (0..K-1) and suffix energies
+};
+
 __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5], int K, int lane,
-                               cpx* s_pole) {
+                               cpx* s_pole, HandoffScratch& hs) {
     const int np = 2 * K;
     if (K < 2) return 0x1p-24f;  // one section: nothing handed on
     if (lane < np) {
@@ -340,13 +350,7 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
     }
     __syncwarp();
     bool bad = false;
-    const int sec = lane >> 1;
-    cpx W[2 * kMaxSections];   // q_ij / (1 - q_ij), j < 2K
-    cpx F[kMaxSections];       // F_i(m)
-#pragma unroll
-    for (int j = 0; j < 2 * kMaxSections; ++j) W[j] = cpx{0.f, 0.f};
-#pragma unroll
-    for (int m = 0; m < kMaxSections; ++m) F[m] = cpx{1.f, 0.f};
+    // lane i < 2K: W[i][j] and F[i][m]
     if (lane < np) {
         const cpx pi = s_pole[lane];
         const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
@@ -354,95 +358,83 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
         const float ir2 = r2 > 1e-24f ? 1.f / r2 : 0.f;
         const cpx inv{pi.re * ir2, -pi.im * ir2};
         const cpx inv2 = cmul(inv, inv);
-#pragma unroll
-        for (int j = 0; j < 2 * kMaxSections; ++j) {
-            if (j < np) {
-                const cpx pj = s_pole[j];
-                const cpx q = cmul(pi, cpx{pj.re, -pj.im});
-                const cpx d{1.f - q.re, -q.im};
-                if (!(fmaf(d.re, d.re, d.im * d.im) > 1e-30f)) bad = true;
-                W[j] = cdiv(q, d);
-            }
+#pragma unroll 1
+        for (int j = 0; j < np; ++j) {
+            const cpx pj = s_pole[j];
+            const cpx q = cmul(pi, cpx{pj.re, -pj.im});
+            const cpx d{1.f - q.re, -q.im};
+            if (!(fmaf(d.re, d.re, d.im * d.im) > 1e-30f)) bad = true;
+            hs.W[lane][j] = cdiv(q, d);
         }
-#pragma unroll
-        for (int m = 0; m < kMaxSections; ++m) {
-            if (m < K) {
-                const float ims = 1.f / num_scale(rowsf[m]);
-                const float b0 = rowsf[m][0] * ims, b1 = rowsf[m][1] * ims, b2 = rowsf[m][2] * ims;
-                cpx f{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int l = 2 * m + u;
-                    if (l != lane) {
-                        const cpx g = cmul(s_pole[l], inv);
-                        const cpx h{1.f - g.re, -g.im};
-                        if (fmaf(h.re, h.re, h.im * h.im) < 1e-8f) bad = true;
-                        f = cdiv(f, h);
-                    }
+#pragma unroll 1
+        for (int m = 0; m < K; ++m) {
+            const float ims = 1.f / num_scale(rowsf[m]);
+            const float b0 = rowsf[m][0] * ims, b1 = rowsf[m][1] * ims, b2 = rowsf[m][2] * ims;
+            cpx f{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
+#pragma unroll 1
+            for (int u = 0; u < 2; ++u) {
+                const int l = 2 * m + u;
+                if (l != lane) {
+                    const cpx g = cmul(s_pole[l], inv);
+                    const cpx h{1.f - g.re, -g.im};
+                    if (fmaf(h.re, h.re, h.im * h.im) < 1e-8f) bad = true;
+                    f = cdiv(f, h);
                 }
-                F[m] = f;
             }
+            hs.F[lane][m] = f;
         }
     }
-    // energy of the cascade whose residue at this lane's pole is R (0 for
-    // poles outside it), with h[0] = h0; false if the sum cancels
-    auto energy = [&](cpx R, float h0, float& E) {
+    __syncwarp();
+    // the energies: cascade t < K is the prefix 0..t, t >= K the suffix
+    // (t - K + 1)..K-1; lane i's residue is the product of its F_i over the
+    // cascade's sections, the pair sum is spread over the whole warp
+    bool ok = true;
+#pragma unroll 1
+    for (int t = 0; t < 2 * K - 1; ++t) {
+        const bool pre = t < K;
+        const int a = pre ? 0 : t - K + 1, b = pre ? t : K - 1;
+        float h0 = 1.f;
+#pragma unroll 1
+        for (int m = a; m <= b; ++m) h0 *= rowsf[m][0] / num_scale(rowsf[m]);
+        if (lane < np) {
+            const int sec = lane >> 1;
+            cpx R{0.f, 0.f};
+            if (sec >= a && sec <= b) {
+                R = cpx{1.f, 0.f};
+#pragma unroll 1
+                for (int m = a; m <= b; ++m) R = cmul(R, hs.F[lane][m]);
+            }
+            hs.R[lane] = R;
+        }
+        __syncwarp();
+        // pair (i, j): lane handles i = lane & 15 and half of the j
         float e = 0.f, ea = 0.f;
-#pragma unroll
-        for (int j = 0; j < 2 * kMaxSections; ++j) {
-            if (j < np) {
-                const cpx Rj{__shfl_sync(0xffffffffu, R.re, j), __shfl_sync(0xffffffffu, R.im, j)};
-                const cpx t = cmul(cmul(R, cpx{Rj.re, -Rj.im}), W[j]);
-                e += t.re;
-                ea += cabs_(t);
+        const int i = lane & 15;
+        if (i < np) {
+            const cpx Ri = hs.R[i];
+#pragma unroll 1
+            for (int j = lane >> 4; j < np; j += 2) {
+                const cpx Rj = hs.R[j];
+                const cpx tt = cmul(cmul(Ri, cpx{Rj.re, -Rj.im}), hs.W[i][j]);
+                e += tt.re;
+                ea += sqrtf(fmaf(tt.re, tt.re, tt.im * tt.im));
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_xor_sync(0xffffffffu, e, o);
             ea += __shfl_xor_sync(0xffffffffu, ea, o);
         }
-        E = fmaf(h0, h0, e);
-        return E > 0.f && E >= 1e-5f * ea && E < 1e30f;
-    };
-    float Epre[kMaxSections], Esuf[kMaxSections];
-    bool ok = true;
-    {
-        // prefixes 0..j
-        cpx P{1.f, 0.f};
-        float h0 = 1.f;
-#pragma unroll
-        for (int j = 0; j < kMaxSections; ++j) {
-            Epre[j] = 1.f;
-            if (j < K) {
-                P = cmul(P, F[j]);
-                h0 *= rowsf[j][0] / num_scale(rowsf[j]);
-                const cpx R = (lane < np && sec <= j) ? P : cpx{0.f, 0.f};
-                ok = energy(R, h0, Epre[j]) && ok;
-            }
-        }
-    }
-    {
-        // suffixes k..K-1
-        cpx P{1.f, 0.f};
-        float h0 = 1.f;
-#pragma unroll
-        for (int k = kMaxSections - 1; k >= 1; --k) {
-            Esuf[k] = 1.f;
-            if (k < K) {
-                P = cmul(P, F[k]);
-                h0 *= rowsf[k][0] / num_scale(rowsf[k]);
-                const cpx R = (lane < np && sec >= k) ? P : cpx{0.f, 0.f};
-                ok = energy(R, h0, Esuf[k]) && ok;
-            }
-        }
-        Esuf[0] = 1.f;
+        const float E = fmaf(h0, h0, e);
+        ok = ok && E > 0.f && E >= 1e-5f * ea && E < 1e30f;
+        if (lane == 0) hs.E[t] = E;
+        __syncwarp();
     }
     if (__any_sync(0xffffffffu, bad) || !ok) return -1.f;
+    // prefix k is E[k]; the suffix starting at section k + 1 is E[K + k]
     float amp = 0.f;
-#pragma unroll
-    for (int k = 0; k + 1 < kMaxSections; ++k)
-        if (k + 1 < K) amp = fmaxf(amp, Epre[k] * Esuf[k + 1]);
-    amp = sqrtf(amp / Epre[K - 1]);
+#pragma unroll 1
+    for (int k = 0; k + 1 < K; ++k) amp = fmaxf(amp, hs.E[k] * hs.E[K + k]);
+    amp = sqrtf(amp / hs.E[K - 1]);
     if (!(amp < 1e30f)) return -1.f;
     return 0x1p-24f * fmaxf(amp, 1.f);
 }
@@ -748,7 +740,8 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         // the precision warp: how much FP32 rounding between sections would
         // cost at the output (released with barrier 2)
         const bool skip = carry_only || (p.flags_opt & kFlagBackwardPlan) || Kc == 0;
-        const float e = skip ? 0.f : handoff_error(s_row, s_rowf, Kc, lane, s_pole2);
+        __shared__ HandoffScratch s_hs;
+        const float e = skip ? 0.f : handoff_error(s_row, s_rowf, Kc, lane, s_pole2, s_hs);
         if (lane == 0) s_handoff = e;
         if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 2)) : "memory");
         return true;
