@@ -173,3 +173,36 @@ def test_differentiation_workload_full_size():
               "a": _rel(gsos[..., 3:], rsos[..., 3:])}
     print(groups)
     assert all(v <= 1e-4 for v in groups.values()), groups
+
+
+def test_adjoint_long_memory_several_segments():
+    """Channels with poles at radius 0.99..0.995 (memory horizons of a few
+    thousand samples) long enough to be cut into many backward segments
+    (each warmed up over its horizon on both sides): every gradient group
+    within 1e-4 of the oracle adjoint, and the plan really cut them."""
+    from synth import filters
+    P = _lib()
+    C, kmax, n = 6, 4, 1 << 19
+    lengths = torch.full((C,), n, dtype=torch.int64)
+    K = torch.full((C,), kmax, dtype=torch.int32)
+    sos = np.zeros((C, kmax, 6))
+    for c in range(C):
+        sos[c] = filters.random_sections(700 + c, kmax, 0.99, 0.995)
+    sos = torch.from_numpy(sos)
+    x = rng.normal(701, rng.STREAM_SIGNAL, C * n)
+    zi = rng.normal(701, rng.STREAM_STATE, C * kmax * 2).view(C, kmax, 2)
+    gy = rng.normal(702, rng.STREAM_SIGNAL, C * n)
+    gzf = rng.normal(703, rng.STREAM_STATE, C * kmax * 2).view(C, kmax, 2)
+    got, ref = run_both(x, sos, K, lengths, zi, gy, gzf)
+    worst = check_grads(got, ref, lengths.numpy(), K.numpy(), 1e-4)
+    # the backward plan's segments: the channel table of the backward
+    # workspace (its channel table follows the header, as in the forward's)
+    plan = P.SosFilter(lengths, kmax)
+    plan.backward(x.cuda(), sos.cuda(), K.cuda(), zi.cuda(), gy.cuda(), gzf.cuda())
+    h = torch.empty(C, dtype=torch.int32)
+    t = torch.empty(C, dtype=torch.int32)
+    st = P._abi.sos_plan_query(plan._bws.data_ptr(), 0, C, h.data_ptr(), t.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    assert (h > 1000).all() and (t >= 4).all(), (h, t)
+    print("long-memory adjoint", worst, "horizons", h.tolist(), "segments", t.tolist())
