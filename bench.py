@@ -442,8 +442,9 @@ def lowpass_leg(P, dev, steps: int = 50):
     ms_b = replay_ms(gb, steps)
     return {"workload": wl.name, "samples": wl.total, "latency_us": ms_s * 1e3,
             "value": wl.total / (ms_s * 1e-3) / 1e9, "unit": "Gsamples/s",
-            "step": "sos_stream: the signal as one block of a stream (one launch, one warp, "
-                    "tables prepared once), one CUDA-graph replay",
+            "step": "sos_stream: the signal as one block of a stream (one launch, tables "
+                    "prepared once, the block cut into warm-up segments within the filter's "
+                    "memory horizon, one warp each), one CUDA-graph replay",
             "latency_us_sos_filter": ms * 1e3,
             "sos_filter_step": "sos_filter (prepare + apply), one CUDA-graph replay",
             "stream_64ch_bp16_256": {"latency_us": ms_b * 1e3,

@@ -219,16 +219,26 @@ sos_status sos_apply_carried(const float *x, int32_t n_channels, int32_t kmax,
 
 /* Low-latency streaming: filters one block of `chunk` new samples of every
  * channel, carrying each channel's state from the previous block, in one
- * kernel launch (one warp per channel, no plan launch, no waits between
- * warps).  The paper's real-time scenario: a signal that arrives in blocks,
- * the state handed from block to block exactly as between groups (Sec. V),
- * the transposed-direct-form-II state of Eq. feedforward_block_uniform's
- * corrections.
+ * kernel launch (no plan launch, no waits between warps).  The paper's
+ * real-time scenario: a signal that arrives in blocks, the state handed from
+ * block to block exactly as between groups (Sec. V), the
+ * transposed-direct-form-II state of Eq. feedforward_block_uniform's
+ * corrections.  A channel within its memory horizon has its block cut into
+ * segments, one warp each, warmed up over the horizon (the first from zi),
+ * so that a long block is not one warp's sequential walk; other channels
+ * take one warp per block.  The segments take zi to be the state this
+ * filter left after earlier samples of the same signals (whose response is
+ * part of the impulse-response tail the horizon bounds).
  *   x, y      device FP32 [n_channels][chunk], channel-major (y must not
  *             overlap x)
- *   state     device FP32 [n_channels][kmax][2], in/out: the state before
- *             this block on entry (zeros for a fresh stream), after it on
- *             return; rows k >= K[c] are left as they are
+ *   zi        device FP32 [n_channels][kmax][2], the state before this block
+ *             (NULL = zero state)
+ *   zf        device FP32 [n_channels][kmax][2], receives the state after it
+ *             (must not overlap zi: alternate two buffers); rows k >= K[c]
+ *             are copied from zi
+ *   flags     SOS_STREAM_FOREIGN_STATE: zi is some other state (a caller's
+ *             initial condition): segments then also start past that
+ *             state's own response; 0 otherwise
  *   workspace a workspace on which sos_prepare has run with the channels'
  *             sos and K, lengths all equal to `chunk`, and the same tuning
  *             (the coefficient tables are reused by every block; prepare
@@ -237,9 +247,10 @@ sos_status sos_apply_carried(const float *x, int32_t n_channels, int32_t kmax,
  * apply as in sos_filter.  Asynchronous on `stream`; argument errors are
  * returned at once.  Consecutive blocks of a stream must be ordered on the
  * GPU (same stream, or events). */
-sos_status sos_stream(const float *x, float *y, float *state, int32_t n_channels, int32_t kmax,
-                      int64_t chunk, void *workspace, size_t ws_bytes, const sos_tuning *tuning,
-                      void *stream);
+#define SOS_STREAM_FOREIGN_STATE 1u
+sos_status sos_stream(const float *x, float *y, const float *zi, float *zf, int32_t n_channels,
+                      int32_t kmax, int64_t chunk, uint32_t flags, void *workspace,
+                      size_t ws_bytes, const sos_tuning *tuning, void *stream);
 
 /* The comparison algorithms of the paper's evaluation (Sec. VIII, beside
  * PH and cyclic reduction), on the same tables and the same parallel

@@ -276,8 +276,8 @@ class SosStream:
         if self.chunk < 1:
             raise ValueError("chunk must be positive")
         if tuning is None:
-            # latency: the smallest group that holds a chunk, N in {16, 32, 64}
-            n = 16 if self.chunk <= 512 else 32
+            # latency: short groups (N = 16) unless the blocks are long
+            n = 16 if self.chunk <= (1 << 14) else 32
             tuning = (n, 8, 1, 0)
         self.plan = SosFilter([self.chunk] * self.n_channels, self.kmax, tuning=tuning,
                               device=sos.device)
@@ -285,10 +285,21 @@ class SosStream:
         self.K = (K if K is not None else
                   torch.full((self.n_channels,), self.kmax, dtype=torch.int32, device=sos.device))
         self.plan.prepare(self.sos, self.K)
-        self.state = torch.zeros((self.n_channels, self.kmax, 2), dtype=torch.float32,
-                                 device=sos.device)
+        # the state alternates between two buffers: each block reads one and
+        # writes the other (different warps of a channel read and write it)
+        self._bufs = [torch.zeros((self.n_channels, self.kmax, 2), dtype=torch.float32,
+                                  device=sos.device) for _ in range(2)]
+        self._cur = 0
+        # a caller's initial state (not one this filter left): the next block
+        # waits for its response to die out before cutting segments
+        self._foreign = zi is not None
         if zi is not None:
             self.state.copy_(zi.reshape(self.n_channels, self.kmax, 2))
+
+    @property
+    def state(self) -> torch.Tensor:
+        """The state after the latest block (before the next one)."""
+        return self._bufs[self._cur]
 
     def __call__(self, x: torch.Tensor, y: Optional[torch.Tensor] = None) -> torch.Tensor:
         _check_device(x, "x")
@@ -298,14 +309,20 @@ class SosStream:
         if y is None:
             y = torch.empty_like(x)
         stream = torch.cuda.current_stream(x.device).cuda_stream
-        st = _abi.sos_stream(x.data_ptr(), y.data_ptr(), self.state.data_ptr(), self.n_channels,
-                             self.kmax, self.chunk, self.plan.workspace.data_ptr(),
-                             self.plan.ws_bytes, self.plan.tuning, stream)
+        zi, zf = self._bufs[self._cur], self._bufs[1 - self._cur]
+        flags = _abi.SOS_STREAM_FOREIGN_STATE if self._foreign else 0
+        st = _abi.sos_stream(x.data_ptr(), y.data_ptr(), zi.data_ptr(), zf.data_ptr(),
+                             self.n_channels, self.kmax, self.chunk, flags,
+                             self.plan.workspace.data_ptr(), self.plan.ws_bytes, self.plan.tuning,
+                             stream)
         if st != 0:
             raise SosError(st, "sos_stream")
+        self._foreign = False
+        self._cur = 1 - self._cur
         return y
 
     def reset(self, zi: Optional[torch.Tensor] = None) -> None:
+        self._foreign = zi is not None
         if zi is None:
             self.state.zero_()
         else:

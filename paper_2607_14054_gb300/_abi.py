@@ -92,7 +92,8 @@ def load(build_if_missing: bool = False):
         lib.sos_apply_baseline.restype = ctypes.c_int
         lib.sos_filtfilt.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, sz, tp, vp]
         lib.sos_filtfilt.restype = ctypes.c_int
-        lib.sos_stream.argtypes = [vp, vp, vp, i32, i32, i64, vp, sz, tp, vp]
+        lib.sos_stream.argtypes = [vp, vp, vp, vp, i32, i32, i64, ctypes.c_uint32, vp, sz, tp,
+                                   vp]
         lib.sos_stream.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
@@ -192,11 +193,16 @@ def sos_filtfilt(x, sos, K, n_channels, kmax, lengths, lengths_host, y, tmp, ws,
                                    V(stream)))
 
 
-def sos_stream(x, y, state, n_channels, kmax, chunk, ws, ws_bytes, tuning, stream) -> int:
-    """All pointer arguments are integers."""
+SOS_STREAM_FOREIGN_STATE = 1
+
+
+def sos_stream(x, y, zi, zf, n_channels, kmax, chunk, flags, ws, ws_bytes, tuning,
+               stream) -> int:
+    """All pointer arguments are integers (0 for NULL)."""
     V = ctypes.c_void_p
-    return int(load().sos_stream(V(x), V(y), V(state), n_channels, kmax, int(chunk), V(ws),
-                                 ws_bytes, _tuning(tuning), V(stream)))
+    return int(load().sos_stream(V(x), V(y), V(zi or None), V(zf or None), n_channels, kmax,
+                                 int(chunk), int(flags), V(ws), ws_bytes, _tuning(tuning),
+                                 V(stream)))
 
 
 def sos_device_status(ws_ptr: int, stream: int) -> int:

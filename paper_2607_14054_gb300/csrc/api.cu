@@ -14,7 +14,8 @@ bool pipe_supported(int N);
 cudaError_t launch_warpseg(const Params& p, int64_t grid, cudaStream_t stream, bool early);
 int warpseg_ctas_per_sm(int N, int algo);
 int warpseg_warps_per_cta();
-cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream);
+cudaError_t launch_stream(const Params& p, int64_t chunk, int64_t seg_len, int32_t maxseg,
+                          int32_t foreign, cudaStream_t stream);
 cudaError_t launch_reverse(const float* src, float* dst, const Params& p, int64_t max_len,
                            cudaStream_t stream);
 cudaError_t launch_compare(const Params& p, int algo, int64_t seg_len, int64_t max_segs,
@@ -313,10 +314,10 @@ sos_status sos_filter(const float* x, const double* sos, const int32_t* K, int32
                      stream);
 }
 
-sos_status sos_stream(const float* x, float* y, float* state, int32_t n_channels, int32_t kmax,
-                      int64_t chunk, void* workspace, size_t ws_bytes, const sos_tuning* tuning,
-                      void* stream) {
-    if (chunk < 0 || n_channels < 1) return SOS_ERR_ARG;
+sos_status sos_stream(const float* x, float* y, const float* zi, float* zf, int32_t n_channels,
+                      int32_t kmax, int64_t chunk, uint32_t flags, void* workspace,
+                      size_t ws_bytes, const sos_tuning* tuning, void* stream) {
+    if (chunk < 0 || n_channels < 1 || (flags & ~SOS_STREAM_FOREIGN_STATE)) return SOS_ERR_ARG;
     if (chunk > 0 && (!x || !y)) return SOS_ERR_ARG;
     // the workspace was carved by sos_prepare for n_channels channels of
     // `chunk` samples each: carve it the same way
@@ -332,12 +333,33 @@ sos_status sos_stream(const float* x, float* y, float* state, int32_t n_channels
         const size_t bytes = sizeof(float) * (size_t)total;
         if (xb < yb + bytes && yb < xb + bytes) return SOS_ERR_ARG;
     }
+    if (zi && zf) {
+        // different warps of one channel read zi and write zf
+        const char* a = reinterpret_cast<const char*>(zi);
+        const char* b = reinterpret_cast<const char*>(zf);
+        const size_t bytes = sizeof(float) * 2 * (size_t)kmax * (size_t)n_channels;
+        if (a < b + bytes && b < a + bytes) return SOS_ERR_ARG;
+    }
     p.x = x;
     p.y = y;
-    p.zi = state;
-    p.zf = state;
+    p.zi = zi;
+    p.zf = zf;
     if (chunk == 0) return SOS_OK;
-    if (launch_stream(p, chunk, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    // segments: enough for every resident warp of the device to take one
+    // when the channels alone do not fill it; each channel's own memory
+    // horizon may lengthen its segments on the device
+    const int64_t group = 32LL * p.N;
+    const int sms = device_sms() > 0 ? device_sms() : 148;
+    const int occ = warpseg_ctas(p.N, 1, 0);
+    const int64_t warps = (int64_t)sms * (occ > 0 ? occ : 1) * warpseg_warps_per_cta();
+    int64_t per = warps / n_channels;
+    if (per < 1) per = 1;
+    int64_t seg = (chunk + per - 1) / per;
+    seg = (seg + group - 1) / group * group;
+    const int64_t maxseg = (chunk + seg - 1) / seg;
+    const int32_t foreign = (flags & SOS_STREAM_FOREIGN_STATE) && zi ? 1 : 0;
+    if (launch_stream(p, chunk, seg, (int32_t)maxseg, foreign,
+                      static_cast<cudaStream_t>(stream)) != cudaSuccess)
         return SOS_ERR_CUDA;
     return SOS_OK;
 }

@@ -444,9 +444,11 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
 // needs it (a segment is at least 2 P and long enough for the initial
 // state's response to decay below the bound, rounded up to whole groups of
 // G), so that long-memory channels keep a bounded warm-up instead of being
-// carried.  -1 where no horizon holds.
+// carried; minseg, the shortest segment the horizon allows.  -1 where no
+// horizon holds.
 __device__ int horizon_combine(bool ok, float h2, int K, int64_t T, int64_t G, float la, float ilr,
-                               float zs, float lr, int64_t& seg) {
+                               float zs, float lr, int64_t& seg, int32_t& minseg,
+                               int32_t& minseg_z) {
     float ptail = ilr != 0.f ? (la + __logf(h2)) * ilr : 0.f;
     // the initial state's response (each pole's share counted 2K times) has
     // decayed below the bound after tz samples
@@ -459,9 +461,16 @@ __device__ int horizon_combine(bool ok, float h2, int K, int64_t T, int64_t G, f
     if (!ok || !(h2 > 0.f) || !(ptail < 1e9f) || !(tz < 1e9f)) return -1;
     const float need = fmaxf(ptail, (float)(2 * K));
     const int64_t P = ((int64_t)ceilf(need) + 15) / 16 * 16;
-    int64_t want = 2 * P > (int64_t)ceilf(tz) ? 2 * P : (int64_t)ceilf(tz);
+    const int64_t itz = (int64_t)ceilf(tz);
+    const int64_t want = 2 * P > itz ? 2 * P : itz;
     seg = T;
     if (want > seg) seg = (want + G - 1) / G * G;
+    // the shortest segments that still start their warm-up inside the
+    // channel, and past an initial state's response (the streaming mode's
+    // segments, where latency, not the warm-up's share, is what counts)
+    const int64_t least = P > itz ? P : itz;
+    minseg = (int32_t)((P + G - 1) / G * G > G ? (P + G - 1) / G * G : G);
+    minseg_z = (int32_t)((least + G - 1) / G * G > G ? (least + G - 1) / G * G : G);
     return (int)P;
 }
 
@@ -710,8 +719,10 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         // conditioned (slow-building responses of poles near the unit circle)
         const float h2 = fmaxf(s_h2, 0.5f * sqrtf(etail));
         int64_t seg = p.seg;
+        int32_t minseg = 0, minseg_z = 0;
         int P = carry_only ? -1
-                           : horizon_combine(ok, h2, Kc, p.seg, 32LL * p.N, la, ilr, zs, lr, seg);
+                           : horizon_combine(ok, h2, Kc, p.seg, 32LL * p.N, la, ilr, zs, lr, seg,
+                                             minseg, minseg_z);
         // backward plans have no look-back: a channel without a horizon is
         // one segment, run from its start to its end by one pipeline
         const int single = (P < 0 && (p.flags_opt & kFlagBackwardPlan)) ? 1 : 0;
@@ -728,6 +739,8 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
             p.chan[c].single = (int16_t)single;
             if (Kc == 0) p.chan[c].ext = 0;  // (else written by the first section warp)
             p.chan[c].seg = P >= 0 ? seg : p.seg;
+            p.chan[c].minseg = P >= 0 ? minseg : 0;
+            p.chan[c].minseg_z = P >= 0 ? minseg_z : 0;
             p.chan[c].ntiles = (int32_t)nt;
             s_horizon = P;
         }

@@ -80,8 +80,12 @@ struct ChanInfo {
                       // (Coef32::misc.w); 3: double-float samples throughout
     int64_t seg;      // segment length of a channel with a horizon (a multiple of 32 N,
                       // at least 2 P)
+    int32_t minseg;   // the shortest segment length the horizon allows (P, whole
+                      // groups), 0 without a horizon
+    int32_t minseg_z; // the same, also long enough for the response of an arbitrary
+                      // initial state to die out
 };
-static_assert(sizeof(ChanInfo) == 56, "channel table entry");
+static_assert(sizeof(ChanInfo) == 64, "channel table entry");
 
 // A channel's memory horizon P is the shortest warm-up after which the
 // cascade's impulse-response tail, summed in absolute value, is below

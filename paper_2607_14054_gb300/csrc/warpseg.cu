@@ -376,35 +376,56 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>()) sos_warpseg_k
     }
 }
 
-// Low-latency streaming: one warp per channel filters the channel's whole
-// chunk (x, y: [C][chunk]) through all K sections, group after group, from
-// the state `p.zi` and leaves the final state in `p.zf` (the same array for
-// in-place state: each warp reads its channel's state before it writes it).
-// No plan launch, no segment hand-out, no waits on other warps: one launch
-// per call, with the coefficient tables of an earlier sos_prepare.  The
-// paper's real-time scenario (a signal arriving in blocks, the state carried
-// from one block to the next, Sec. V's group chaining across calls).
+// Low-latency streaming: the next block of `chunk` samples of every channel
+// (x, y: [C][chunk]) through all K sections, from the state `p.zi` into the
+// state `p.zf`, in one launch with the coefficient tables of an earlier
+// sos_prepare.  Warp w takes segment w % maxseg of channel w / maxseg: a
+// channel within its memory horizon is cut into segments of
+// max(seg_len, its shortest allowed segment) samples, each warmed up over the
+// horizon from zero state (the first from the incoming state), so that a
+// long block is not one warp's sequential walk; other channels are one
+// segment.  No plan launch, no hand-out counter, no waits on other warps.
+// The paper's real-time scenario: a signal arriving in blocks, the state
+// carried from one block to the next (Sec. V's group chaining across calls).
 template <int N>
 __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>())
-    sos_stream_kernel(Params p, int64_t chunk) {
+    sos_stream_kernel(Params p, int64_t chunk, int64_t seg_len, int32_t maxseg, int32_t foreign) {
     using WC = WsCfg<N>;
     extern __shared__ float4 s_ws4[];
     __shared__ float4 s_z[kWsWarps][kMaxSections];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int c = (int)blockIdx.x * kWsWarps + w;
+    const int64_t gw = (int64_t)blockIdx.x * kWsWarps + w;
+    const int c = (int)(gw / maxseg);
+    const int si = (int)(gw % maxseg);
     if (c >= p.C || chunk <= 0) return;
+    const ChanInfo ci = p.chan[c];
+    int64_t seg = chunk;
+    if (ci.horizon >= 0 && ci.K > 0) {
+        // the incoming state of a stream is what earlier samples of the same
+        // signal left, so its response is part of the impulse-response tail
+        // the horizon bounds; a foreign initial state also has to die out
+        const int64_t least = foreign ? ci.minseg_z : ci.minseg;
+        seg = seg_len > least ? seg_len : least;
+        if (seg > chunk) seg = chunk;
+    }
+    const int nseg = (int)((chunk + seg - 1) / seg);
+    if (si >= nseg) return;
+    // state rows past K (or a channel without sections) pass through
+    if (si == 0 && p.zf)
+        for (int i = ci.K * 2 + lane; i < p.kmax * 2; i += 32)
+            p.zf[(int64_t)c * p.kmax * 2 + i] = p.zi ? p.zi[(int64_t)c * p.kmax * 2 + i] : 0.f;
     float* slots = reinterpret_cast<float*>(s_ws4) + (size_t)w * 2 * WC::kSlot;
     SegGeom sg;
     sg.c = c;
-    sg.si = 0;
+    sg.si = si;
     sg.off = (int64_t)c * chunk;
     sg.len = chunk;
-    sg.out_lo = 0;
-    sg.out_hi = chunk;
-    sg.cstart = 0;
-    sg.ngroups = (int)((chunk + WC::kGroup - 1) / WC::kGroup);
-    sg.horizon = 0;
-    sg.K = p.chan[c].K;
+    sg.out_lo = (int64_t)si * seg;
+    sg.out_hi = sg.out_lo + seg < chunk ? sg.out_lo + seg : chunk;
+    sg.cstart = si == 0 ? 0 : sg.out_lo - ci.horizon;
+    sg.ngroups = (int)((sg.out_hi - sg.cstart + WC::kGroup - 1) / WC::kGroup);
+    sg.horizon = ci.horizon;
+    sg.K = ci.K;
     int cur = 0;
     bool pending = false;
     ws_run_segment<N, false>(p, sg, slots, s_z[w], lane, cur, pending, nullptr, 0);
@@ -442,7 +463,8 @@ int warpseg_ctas_per_sm(int N, int algo) {
 
 int warpseg_warps_per_cta() { return kWsWarps; }
 
-cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream) {
+cudaError_t launch_stream(const Params& p, int64_t chunk, int64_t seg_len, int32_t maxseg,
+                          int32_t foreign, cudaStream_t stream) {
     const void* fn = p.N == 16 ? reinterpret_cast<const void*>(&sos_stream_kernel<16>)
                    : p.N == 32 ? reinterpret_cast<const void*>(&sos_stream_kernel<32>)
                                : reinterpret_cast<const void*>(&sos_stream_kernel<64>);
@@ -454,8 +476,9 @@ cudaError_t launch_stream(const Params& p, int64_t chunk, cudaStream_t stream) {
         if (e != cudaSuccess) return e;
         attr[idx] = true;
     }
-    void* args[] = {const_cast<Params*>(&p), &chunk};
-    const unsigned grid = (unsigned)((p.C + kWsWarps - 1) / kWsWarps);
+    void* args[] = {const_cast<Params*>(&p), &chunk, &seg_len, &maxseg, &foreign};
+    const int64_t warps = (int64_t)p.C * maxseg;
+    const unsigned grid = (unsigned)((warps + kWsWarps - 1) / kWsWarps);
     return cudaLaunchKernel(fn, dim3(grid), dim3(kWsThreads), args, ws_smem(p.N), stream);
 }
 

@@ -83,9 +83,35 @@ def test_stream_rejects_bad_arguments():
     st = P.SosStream(wl.sos.cuda(), 256)
     with pytest.raises(ValueError):
         st(torch.zeros(255, device="cuda"))
-    # overlapping x and y
+    # overlapping x and y, or zi and zf
     buf = torch.zeros(512, device="cuda")
     stream = torch.cuda.current_stream().cuda_stream
-    r = P._abi.sos_stream(buf.data_ptr(), buf.data_ptr() + 4, st.state.data_ptr(), 1, 1, 256,
+    r = P._abi.sos_stream(buf.data_ptr(), buf.data_ptr() + 4, st.state.data_ptr(), 0, 1, 1, 256,
+                          0, st.plan.workspace.data_ptr(), st.plan.ws_bytes, st.plan.tuning,
+                          stream)
+    assert r == -1
+    r = P._abi.sos_stream(buf.data_ptr(), buf.data_ptr() + 2048, st.state.data_ptr(),
+                          st.state.data_ptr(), 1, 1, 256, 0, st.plan.workspace.data_ptr(),
+                          st.plan.ws_bytes, st.plan.tuning, stream)
+    assert r == -1
+    # unknown flags
+    r = P._abi.sos_stream(buf.data_ptr(), buf.data_ptr() + 2048, 0, 0, 1, 1, 256, 6,
                           st.plan.workspace.data_ptr(), st.plan.ws_bytes, st.plan.tuning, stream)
     assert r == -1
+
+
+def test_stream_long_blocks_cut_into_segments():
+    """Blocks of 2^17 samples of short-memory channels, cut into several
+    warm-up segments per block inside one launch, three blocks in a row
+    against the one-shot oracle (the state handed between blocks)."""
+    P = _lib()
+    C, chunk = 3, 1 << 17
+    T = 3 * chunk
+    x, sos, K, L, zi = random_case(95, [T] * C, 4, rmax=0.9)
+    y, state = _stream(P, x.view(C, T).cuda(), sos, K, zi, chunk, (32, 8, 1, 0))
+    y_ref, zf_ref = oracle.sosfilt(x.double().numpy(), sos.numpy(), K=K.numpy(),
+                                   lengths=L.numpy(), zi=zi.double().numpy())
+    zf = state.cpu().numpy().copy()
+    for c in range(C):
+        zf[c, int(K[c]):] = 0.0
+    check(y.reshape(-1).cpu().numpy(), zf, y_ref, zf_ref, L.numpy(), K.numpy(), 1e-5)
