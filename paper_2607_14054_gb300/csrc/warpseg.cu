@@ -410,6 +410,15 @@ __global__ void __launch_bounds__(kWsThreads, ws_ctas_per_sm<N>())
     }
     const int nseg = (int)((chunk + seg - 1) / seg);
     if (si >= nseg) return;
+    // the channel's coefficient tables into L1 now, all sections at once
+    // (each is otherwise a round trip to L2 at the section's first use, one
+    // after another: most of a short block's latency)
+    {
+        const char* cb = reinterpret_cast<const char*>(p.c32 + (int64_t)c * p.kmax);
+        const int lines = (int)((sizeof(Coef32) * (size_t)ci.K + 127) / 128);
+        for (int i = lane; i < lines; i += 32)
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(cb + 128 * (size_t)i));
+    }
     // state rows past K (or a channel without sections) pass through
     if (si == 0 && p.zf)
         for (int i = ci.K * 2 + lane; i < p.kmax * 2; i += 32)
