@@ -385,12 +385,15 @@ sos_status sos_plan_query(void *workspace, int32_t first, int32_t count, int32_t
  *   2  some section also runs its lane scan and fold (S4) in double-float
  *      (the largest entry of its transition powers A^(N 2^j), A^(N l) exceeds
  *      8, or the displacement exceeds 1e-4);
- *   3  the whole cascade runs with double-float samples (about 44 bits): the
- *      plan's estimate of the error that FP32 rounding of the signals handed
- *      between sections would cause at the output (white input, from the
- *      norms of the partial cascades by partial fractions) or of a section's
- *      own rounding (its condition number ||g|| ||b|| / ||h||) exceeds 2^-17,
- *      or SOS_FLAG_DOUBLE_FLOAT was given.
+ *   3  sections run with double-float samples (about 44 bits): the plan's
+ *      estimate of the error that FP32 rounding of the signal handed from
+ *      section k to k + 1 would cause at the output (white input, from the
+ *      norms of the partial cascades by partial fractions) exceeds 2^-15 for
+ *      some k, or a section's own rounding (its condition number
+ *      ||g|| ||b|| / ||h||) exceeds 2^-17.  The double-float range spans
+ *      both sides of every such hand-off and every such section; the
+ *      sections outside it run in FP32 (the whole cascade when the estimate
+ *      is unreliable or SOS_FLAG_DOUBLE_FLOAT was given).
  * Classes 1..3 take effect on the warp-segment kernel (the default for
  * channels within their memory horizon); the section pipeline
  * (SOS_FLAG_SECTION_PIPELINE), the cyclic-reduction solver and the look-back

@@ -332,8 +332,10 @@ struct HandoffScratch {
 };
 
 __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5], int K, int lane,
-                               cpx* s_pole, HandoffScratch& hs) {
+                               cpx* s_pole, HandoffScratch& hs, int& blo, int& bhi) {
     const int np = 2 * K;
+    blo = K;
+    bhi = -1;
     if (K < 2) return 0x1p-24f;  // one section: nothing handed on
     if (lane < np) {
         const double a1 = rows[lane >> 1][3], a2 = rows[lane >> 1][4];
@@ -430,10 +432,18 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
         __syncwarp();
     }
     if (__any_sync(0xffffffffu, bad) || !ok) return -1.f;
-    // prefix k is E[k]; the suffix starting at section k + 1 is E[K + k]
+    // prefix k is E[k]; the suffix starting at section k + 1 is E[K + k];
+    // the hand-offs whose own estimate is above the bound: [blo, bhi]
     float amp = 0.f;
 #pragma unroll 1
-    for (int k = 0; k + 1 < K; ++k) amp = fmaxf(amp, hs.E[k] * hs.E[K + k]);
+    for (int k = 0; k + 1 < K; ++k) {
+        const float a = hs.E[k] * hs.E[K + k];
+        amp = fmaxf(amp, a);
+        if (0x1p-24f * sqrtf(a / hs.E[K - 1]) > kHandOffErrMax) {
+            blo = min(blo, k);
+            bhi = k;
+        }
+    }
     amp = sqrtf(amp / hs.E[K - 1]);
     if (!(amp < 1e30f)) return -1.f;
     return 0x1p-24f * fmaxf(amp, 1.f);
@@ -567,6 +577,7 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
     __shared__ float s_dfscan[kMaxSections];    // the section's precision level (misc.w)
     __shared__ float s_kappa[kMaxSections];     // section_kappa()
     __shared__ float s_handoff;                 // handoff_error(), -1 if unknown
+    __shared__ int s_blo, s_bhi;                // the hand-offs it blames (first, last)
     __shared__ double s_b0inv[kMaxSections];    // 1 / b0 (normalised), 0 if b0 = 0
     __shared__ float s_h2;                      // ||h||_2 lower bound
     __shared__ int s_mode, s_horizon, s_err;
@@ -754,8 +765,14 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         // cost at the output (released with barrier 2)
         const bool skip = carry_only || (p.flags_opt & kFlagBackwardPlan) || Kc == 0;
         __shared__ HandoffScratch s_hs;
-        const float e = skip ? 0.f : handoff_error(s_row, s_rowf, Kc, lane, s_pole2, s_hs);
-        if (lane == 0) s_handoff = e;
+        int blo = Kc, bhi = -1;
+        const float e =
+            skip ? 0.f : handoff_error(s_row, s_rowf, Kc, lane, s_pole2, s_hs, blo, bhi);
+        if (lane == 0) {
+            s_handoff = e;
+            s_blo = blo;
+            s_bhi = bhi;
+        }
         if (Kc > 0) asm volatile("bar.arrive 2, %0;" ::"r"(32 * (Kc + 2)) : "memory");
         return true;
     }
@@ -861,15 +878,31 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         // ill-conditioned (kappa), or when the call asks for it
         int16_t e = 0;
         float kap = 0.f;
+        // the double-float range: the sections on both sides of every
+        // hand-off the estimate blames (the signal there has to be handed on
+        // beyond FP32, so it is computed in double-float up to it and taken in
+        // double-float after it) and every ill-conditioned section; all of
+        // them when the estimate is unreliable or the call asks for it
+        int lo = s_bhi >= 0 ? s_blo : Kc, hi = s_bhi >= 0 ? s_bhi + 1 : -1;
         for (int j = 0; j < Kc; ++j) {
             e = (int16_t)max((int)e, (int)s_dfscan[j]);
             kap = fmaxf(kap, s_kappa[j]);
+            if (!(s_kappa[j] * 0x1p-24f <= kSectionErrMax)) {
+                lo = min(lo, j);
+                hi = max(hi, j);
+            }
         }
         const float h = s_handoff;
-        const bool whole = (p.flags_opt & SOS_FLAG_DOUBLE_FLOAT) || h > kHandOffErrMax ||
-                           (h < 0.f && e >= 2) || !(kap * 0x1p-24f <= kSectionErrMax);
+        const bool all = (p.flags_opt & SOS_FLAG_DOUBLE_FLOAT) || (h < 0.f && e >= 2);
+        const bool whole = all || h > kHandOffErrMax || !(kap * 0x1p-24f <= kSectionErrMax);
+        if (all || hi < lo) {
+            lo = 0;
+            hi = Kc - 1;
+        }
         if (whole && s_horizon >= 0 && !(p.flags_opt & kFlagBackwardPlan)) e = 3;
         p.chan[c].ext = e;
+        p.chan[c].dflo = (int16_t)(e == 3 ? lo : 0);
+        p.chan[c].dfhi = (int16_t)(e == 3 ? hi : Kc - 1);
     }
     if (s_horizon >= 0) return true;
     if (lane == 0) {

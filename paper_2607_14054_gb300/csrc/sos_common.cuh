@@ -84,8 +84,11 @@ struct ChanInfo {
                       // groups), 0 without a horizon
     int32_t minseg_z; // the same, also long enough for the response of an arbitrary
                       // initial state to die out
+    int16_t dflo, dfhi;  // precision class 3: sections dflo..dfhi run with double-float
+                         // samples, the others in FP32
+    int32_t pad;
 };
-static_assert(sizeof(ChanInfo) == 64, "channel table entry");
+static_assert(sizeof(ChanInfo) == 72, "channel table entry");
 
 // A channel's memory horizon P is the shortest warm-up after which the
 // cascade's impulse-response tail, summed in absolute value, is below

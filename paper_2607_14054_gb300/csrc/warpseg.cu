@@ -69,7 +69,8 @@ enum WsPrec {
     kPrecSect = 1,  // sections flagged in Coef32::misc.w: 1 = coefficient low
                     // parts in the in-lane recursions, 2 = also the lane scan and
                     // fold in double-float
-    kPrecDF = 2     // the whole cascade with double-float samples
+    kPrecDF = 2     // a range of sections with double-float samples (ChanInfo::dflo..dfhi),
+                    // FP32 around it
 };
 
 // The section coefficients of a channel run with double-float samples.
@@ -79,14 +80,14 @@ __device__ __forceinline__ SecDF load_secdf(const Coef32* cf) {
                  df{br.z, bl.z}};
 }
 
-// All K sections of a channel run with double-float samples over one group
-// (kPrecDF): on entry the lane's row holds its chunk of the group's FP32
-// input, on exit the chunk of the output, rounded once.  Out of line, so
+// Sections [k0, k1) of a channel run with double-float samples over one
+// group (kPrecDF): on entry the lane's row holds its chunk of the range's
+// FP32 input, on exit the chunk of its output, rounded once.  Out of line, so
 // that its register needs (a double-float section keeps several times the
 // temporaries of an FP32 one) do not reach the allocation of the FP32 code
 // in the same kernel; the call costs nothing next to the section's work.
 template <int N, bool ZF>
-__device__ __noinline__ void dfx_group(const Params& p, const Coef32* cf0, int K, int c,
+__device__ __noinline__ void dfx_group(const Params& p, const Coef32* cf0, int k0, int k1, int c,
                                        float* row, float4* zs, int lane, int owner, int mq) {
     float v[N];
     row_to_chunk<N>(v, row);
@@ -96,7 +97,7 @@ __device__ __noinline__ void dfx_group(const Params& p, const Coef32* cf0, int K
     for (int b = 0; b < N / 4; ++b)
         reinterpret_cast<float4*>(row)[b] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll 1
-    for (int k = 0; k < K; ++k) {
+    for (int k = k0; k < k1; ++k) {
         const Coef32* cf = cf0 + k;
         const SecDF sd = load_secdf(cf);
         const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane];
@@ -112,6 +113,61 @@ __device__ __noinline__ void dfx_group(const Params& p, const Coef32* cf0, int K
         const float4 l = reinterpret_cast<const float4*>(row)[b];
         reinterpret_cast<float4*>(row)[b] = make_float4(v[4 * b + 0] + l.x, v[4 * b + 1] + l.y,
                                                         v[4 * b + 2] + l.z, v[4 * b + 3] + l.w);
+    }
+}
+
+// Sections [k0, k1) of a channel over one group in FP32, the chunk v[] in
+// registers; zs: their DF2T states (lo parts left zero).  One copy of the
+// section code (a rolled loop keeps the kernel's instruction footprint inside
+// the instruction cache); plain (L1-cached) loads at the point of use:
+// read-only loads would be hoisted out of the group loop, eight sections'
+// worth of live registers.  PREC = kPrecSect: each section's level
+// (Coef32::misc.w) picks the coefficient low parts or the double-float scan.
+// RAW: b0, b1, b2 normalised by a0 only (the double-float range's
+// neighbours, whose states are not scaled by the factored gains).
+template <int N, bool FACT, bool CR, bool ZF, int PREC, bool RAW>
+__device__ __forceinline__ void ws_sections(const Params& p, int c, const Coef32* cf0, int k0,
+                                            int k1, float (&v)[N], float* row, float4* zs,
+                                            int lane, int owner, int mq) {
+#pragma unroll 1
+    for (int k = k0; k < k1; ++k) {
+        const Coef32* cf = cf0 + k;
+        float4 ab = cf->ab;
+        float b0 = FACT ? 1.f : cf->misc.x;
+        if (RAW) {
+            const float4 br = cf->braw;
+            ab.z = br.y;
+            ab.w = br.z;
+            b0 = br.x;
+        }
+        const float G = (ZF && FACT) ? cf->misc.y : 1.f;
+        float* zf_dst = ZF ? p.zf + ((int64_t)c * p.kmax + k) * 2 : nullptr;
+        const float4 zz = zs[k];
+        float2 z = make_float2(zz.x, zz.z);
+        const float lvl = PREC == kPrecSect ? cf->misc.w : 0.f;
+        if (CR) {
+            pipe_section_cr<N, FACT, ZF>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, lane == owner, mq,
+                                         row, zf_dst, G);
+        } else if (PREC == kPrecSect && lvl > 1.5f) {
+            const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane], alo = cf->alo;
+            pipe_section<N, FACT, ZF, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
+                                                   lane == owner, mq, row, zf_dst, G, -1, 0.f,
+                                                   0.f, cf->phi_lo, lpl,
+                                                   make_float2(alo.x, alo.y));
+        } else if (PREC == kPrecSect && lvl > 0.5f) {
+            const float4 lp = cf->lane_pow[lane], alo = cf->alo;
+            pipe_section<N, FACT, ZF, false, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
+                                                          lane == owner, mq, row, zf_dst, G, -1,
+                                                          0.f, 0.f, nullptr,
+                                                          make_float4(0.f, 0.f, 0.f, 0.f),
+                                                          make_float2(alo.x, alo.y));
+        } else {
+            const float4 lp = cf->lane_pow[lane];
+            pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
+                                      row, zf_dst, G);
+        }
+        // every lane holds the outgoing state; the writes agree
+        if (lane == 0) zs[k] = make_float4(z.x, 0.f, z.y, 0.f);
     }
 }
 
@@ -148,48 +204,23 @@ __device__ __forceinline__ void ws_group(const Params& p, const SegGeom& sg, flo
     float* row = slot + lane * SL::kRow;
     float v[N];
     if (PREC == kPrecDF) {
-        dfx_group<N, ZF>(p, cf0, K, sg.c, row, zs, lane, owner, mq);
+        // FP32 sections before and after the double-float range (their b
+        // coefficients unfactored, like the range's), the range itself with
+        // double-float samples
+        const ChanInfo& ci = p.chan[sg.c];
+        const int dlo = ci.dflo, dhi = ci.dfhi;
         row_to_chunk<N>(v, row);
+        ws_sections<N, false, false, ZF, kPrecSect, true>(p, sg.c, cf0, 0, dlo, v, row, zs,
+                                                           lane, owner, mq);
+        chunk_to_row<N>(v, row);
+        dfx_group<N, ZF>(p, cf0, dlo, dhi + 1, sg.c, row, zs, lane, owner, mq);
+        row_to_chunk<N>(v, row);
+        ws_sections<N, false, false, ZF, kPrecSect, true>(p, sg.c, cf0, dhi + 1, K, v, row, zs,
+                                                           lane, owner, mq);
     } else {
-    row_to_chunk<N>(v, row);
-    // one copy of the section code (a rolled loop keeps the kernel's
-    // instruction footprint inside the instruction cache); plain (L1-cached)
-    // loads at the point of use: read-only loads would be hoisted out of the
-    // group loop, eight sections' worth of live registers
-#pragma unroll 1
-    for (int k = 0; k < K; ++k) {
-        const Coef32* cf = cf0 + k;
-        const float4 ab = cf->ab;
-        const float b0 = FACT ? 1.f : cf->misc.x;
-        const float G = (ZF && FACT) ? cf->misc.y : 1.f;
-        float* zf_dst = ZF ? p.zf + ((int64_t)sg.c * p.kmax + k) * 2 : nullptr;
-        const float4 zz = zs[k];
-        float2 z = make_float2(zz.x, zz.z);
-        const float lvl = PREC == kPrecSect ? cf->misc.w : 0.f;
-        if (CR) {
-            pipe_section_cr<N, FACT, ZF>(v, ab, b0, &cf->cr_lv[0], z.x, z.y, lane == owner, mq,
-                                         row, zf_dst, G);
-        } else if (PREC == kPrecSect && lvl > 1.5f) {
-            const float4 lp = cf->lane_pow[lane], lpl = cf->lane_lo[lane], alo = cf->alo;
-            pipe_section<N, FACT, ZF, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
-                                                   lane == owner, mq, row, zf_dst, G, -1, 0.f,
-                                                   0.f, cf->phi_lo, lpl,
-                                                   make_float2(alo.x, alo.y));
-        } else if (PREC == kPrecSect && lvl > 0.5f) {
-            const float4 lp = cf->lane_pow[lane], alo = cf->alo;
-            pipe_section<N, FACT, ZF, false, false, true>(v, ab, b0, cf->phi_pow, lp, z.x, z.y,
-                                                          lane == owner, mq, row, zf_dst, G, -1,
-                                                          0.f, 0.f, nullptr,
-                                                          make_float4(0.f, 0.f, 0.f, 0.f),
-                                                          make_float2(alo.x, alo.y));
-        } else {
-            const float4 lp = cf->lane_pow[lane];
-            pipe_section<N, FACT, ZF>(v, ab, b0, cf->phi_pow, lp, z.x, z.y, lane == owner, mq,
-                                      row, zf_dst, G);
-        }
-        // every lane holds the outgoing state; the writes agree
-        if (lane == 0) zs[k] = make_float4(z.x, 0.f, z.y, 0.f);
-    }
+        row_to_chunk<N>(v, row);
+        ws_sections<N, FACT, CR, ZF, PREC, false>(p, sg.c, cf0, 0, K, v, row, zs, lane, owner,
+                                                  mq);
     }
     if (FACT) {
         const float Gk = cf0[K - 1].misc.y;
