@@ -252,6 +252,38 @@ sos_status sos_stream(const float *x, float *y, const float *zi, float *zf, int3
                       int32_t kmax, int64_t chunk, uint32_t flags, void *workspace,
                       size_t ws_bytes, const sos_tuning *tuning, void *stream);
 
+/* The whole call from host memory to host memory: sos_filter on a signal in
+ * (pinned) host memory, returning the output there.  The packed signal is cut
+ * into blocks of at most `block` samples (whole channels grouped up to it; a
+ * longer channel in time pieces whose DF2T states are handed from piece to
+ * piece on the device, as between groups, Sec. V); for each block the copy in
+ * (a library-owned stream), the filter (sos_filter on `stream`) and the copy
+ * out (a second library-owned stream) are ordered by events through two
+ * device buffers per direction, so that the copies in and out and the
+ * filtering overlap.
+ *   x_host, y_host  host FP32, packed as in sos_filter; pinned memory for the
+ *                   copies to overlap (pageable memory works, serialised)
+ *   sos, K, lengths, zi, zf   device arrays as in sos_filter
+ *   workspace       device scratch of at least *ws_bytes of
+ *                   sos_filter_host_sizes, initialised by sos_workspace_init
+ *   staging         device buffer of at least *staging_bytes (the block
+ *                   buffers, the state hand-off, two length cells)
+ *   block           samples per block (<= 0: an eighth of the signal, at
+ *                   least 2^20)
+ * Asynchronous on `stream`: y_host holds the output once `stream` has
+ * completed the call's work.  SOS_ERR_WORKSPACE if a buffer is too small;
+ * refused (SOS_ERR_ARG) while `stream` is being captured.  Calls on one
+ * device enqueue in turn (a library mutex); their copies share the library's
+ * two copy streams. */
+sos_status sos_filter_host_sizes(int32_t n_channels, int32_t kmax, const int64_t *lengths_host,
+                                 int64_t block, const sos_tuning *tuning, size_t *ws_bytes,
+                                 size_t *staging_bytes, int64_t *block_used);
+sos_status sos_filter_host(const float *x_host, const double *sos, const int32_t *K,
+                           int32_t n_channels, int32_t kmax, const int64_t *lengths,
+                           const int64_t *lengths_host, const float *zi, float *y_host, float *zf,
+                           void *workspace, size_t ws_bytes, void *staging, size_t staging_bytes,
+                           int64_t block, const sos_tuning *tuning, void *stream);
+
 /* The comparison algorithms of the paper's evaluation (Sec. VIII, beside
  * PH and cyclic reduction), on the same tables and the same parallel
  * decomposition: each channel cut into segments of seg_len outputs (>= 32),

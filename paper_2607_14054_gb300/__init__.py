@@ -21,7 +21,7 @@ import torch
 from . import _abi
 from ._abi import SosError, sos_tuning  # noqa: F401
 
-__all__ = ["SosFilter", "SosStream", "sosfilt", "sosfiltfilt", "sosfilt_diff", "SosFilterFunction", "SosError",
+__all__ = ["SosFilter", "SosHostFilter", "SosStream", "sosfilt", "sosfilt_host", "sosfiltfilt", "sosfilt_diff", "SosFilterFunction", "SosError",
            "sos_tuning", "build"]
 
 
@@ -364,6 +364,110 @@ def sosfilt(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None
         if st != 0:
             raise SosError(st, "sos_filter (device)")
     return y, zf
+
+
+class SosHostFilter:
+    """sos_filter from host memory to host memory (``sos_filter_host``): the
+    signal is cut into blocks whose copy in, filtering and copy out overlap.
+    Keeps the device workspace and staging buffers for repeated calls with
+    the same channel lengths."""
+
+    def __init__(self, lengths: Sequence[int] | torch.Tensor, kmax: int,
+                 tuning: Optional[Sequence[int]] = None, block: int = 0, device=None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("sosfilt needs a CUDA device")
+        _abi.load()
+        self.device = torch.device(device if device is not None else "cuda")
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        lh = torch.as_tensor(lengths, dtype=torch.int64).reshape(-1).cpu().contiguous()
+        if lh.numel() < 1 or int(lh.min()) < 0:
+            raise ValueError("lengths must be one or more non-negative counts")
+        self.lengths_host = lh
+        self.lengths = lh.to(self.device)
+        self.n_channels = int(lh.numel())
+        self.kmax = int(kmax)
+        self.total = int(lh.sum())
+        self.tuning = tuple(tuning) if tuning is not None else (0, 0, 0, 0)
+        st, ws, stg, blk = _abi.sos_filter_host_sizes(self.n_channels, self.kmax, lh.data_ptr(),
+                                                      block, self.tuning)
+        if st != 0:
+            raise SosError(st, "sos_filter_host_sizes")
+        self.block = blk
+        self.ws_bytes, self.staging_bytes = ws, stg
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.staging = torch.empty(stg, dtype=torch.uint8, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = _abi.sos_workspace_init(self.workspace.data_ptr(), ws, stream)
+        if st != 0:
+            raise SosError(st, "sos_workspace_init")
+
+    def __call__(self, x_host: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                 zi: Optional[torch.Tensor] = None, y_host: Optional[torch.Tensor] = None,
+                 zf: Optional[torch.Tensor] = None, want_zf: bool = True):
+        """x_host: float32 host tensor (pinned for the copies to overlap);
+        sos, K, zi on the device.  Returns (y_host, zf); y_host is complete
+        once the current stream has finished the call."""
+        C, kmax = self.n_channels, self.kmax
+        if x_host.is_cuda or x_host.dtype != torch.float32 or not x_host.is_contiguous() or \
+                x_host.numel() != self.total:
+            raise ValueError("x_host must be a contiguous float32 host tensor of sum(lengths)")
+        sos = sos.reshape(C, kmax, 6)
+        if sos.dtype != torch.float64 or not sos.is_contiguous() or sos.device != self.device:
+            raise ValueError("sos must be contiguous float64 [C, kmax, 6] on the plan's device")
+        if K is None:
+            K = torch.full((C,), kmax, dtype=torch.int32, device=self.device)
+        if zi is not None:
+            zi = zi.reshape(C, kmax, 2)
+            if zi.dtype != torch.float32 or not zi.is_contiguous() or zi.device != self.device:
+                raise ValueError("zi must be contiguous float32 [C, kmax, 2] on the device")
+        if y_host is None:
+            y_host = torch.empty(self.total, dtype=torch.float32, pin_memory=True)
+        if y_host.is_cuda or y_host.numel() != self.total or not y_host.is_contiguous():
+            raise ValueError("y_host must be a contiguous float32 host tensor of sum(lengths)")
+        if zf is None and want_zf:
+            zf = torch.empty((C, kmax, 2), dtype=torch.float32, device=self.device)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        st = _abi.sos_filter_host(x_host.data_ptr(), sos.data_ptr(), K.data_ptr(), C, kmax,
+                                  self.lengths.data_ptr(), self.lengths_host.data_ptr(),
+                                  zi.data_ptr() if zi is not None else 0, y_host.data_ptr(),
+                                  zf.data_ptr() if zf is not None else 0,
+                                  self.workspace.data_ptr(), self.ws_bytes,
+                                  self.staging.data_ptr(), self.staging_bytes, self.block,
+                                  self.tuning, stream)
+        if st != 0:
+            raise SosError(st, "sos_filter_host")
+        return y_host, zf
+
+
+_host_plans = {}
+
+
+def sosfilt_host(x_host: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
+                 lengths=None, zi: Optional[torch.Tensor] = None,
+                 y_host: Optional[torch.Tensor] = None, tuning=None, block: int = 0):
+    """``sosfilt`` for a signal in host memory (``sos_filter_host``): x_host
+    float32 on the host (pinned), sos/K/zi on the CUDA device.  Returns
+    (y_host, zf) after synchronising the current stream, so y_host is ready."""
+    if sos.dim() == 2:
+        sos = sos.unsqueeze(0)
+    _check_device(sos, "sos")
+    C, kmax = int(sos.shape[0]), int(sos.shape[1])
+    if lengths is None:
+        if C != 1:
+            raise ValueError("lengths are required for more than one channel")
+        lengths = [x_host.numel()]
+    lh = tuple(int(v) for v in torch.as_tensor(lengths).reshape(-1).tolist())
+    key = (sos.device, lh, kmax, tuple(tuning) if tuning is not None else None, int(block))
+    plan = _host_plans.get(key)
+    if plan is None:
+        plan = SosHostFilter(lh, kmax, tuning=tuning, block=block, device=sos.device)
+        if len(_host_plans) > 8:
+            _host_plans.clear()
+        _host_plans[key] = plan
+    y_host, zf = plan(x_host.contiguous(), sos.contiguous(), K, zi, y_host=y_host)
+    torch.cuda.current_stream(sos.device).synchronize()
+    return y_host, zf
 
 
 class SosFilterFunction(torch.autograd.Function):

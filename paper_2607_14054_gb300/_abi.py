@@ -95,6 +95,11 @@ def load(build_if_missing: bool = False):
         lib.sos_stream.argtypes = [vp, vp, vp, vp, i32, i32, i64, ctypes.c_uint32, vp, sz, tp,
                                    vp]
         lib.sos_stream.restype = ctypes.c_int
+        lib.sos_filter_host_sizes.argtypes = [i32, i32, vp, i64, tp, vp, vp, vp]
+        lib.sos_filter_host_sizes.restype = ctypes.c_int
+        lib.sos_filter_host.argtypes = [vp, vp, vp, i32, i32, vp, vp, vp, vp, vp, vp, sz, vp, sz,
+                                        i64, tp, vp]
+        lib.sos_filter_host.restype = ctypes.c_int
         lib.sos_device_status.argtypes = [vp, vp]
         lib.sos_device_status.restype = ctypes.c_int
         lib.sos_backward_workspace_size.argtypes = [i32, i32, vp, tp]
@@ -139,6 +144,27 @@ def sos_filter(x, sos, K, n_channels, kmax, lengths, lengths_host, zi, y, zf, ws
     return int(load().sos_filter(V(x), V(sos), V(K), n_channels, kmax, V(lengths), V(lengths_host),
                                  V(zi or None), V(y), V(zf or None), V(ws), ws_bytes,
                                  _tuning(tuning), V(stream)))
+
+
+def sos_filter_host_sizes(n_channels, kmax, lengths_host, block, tuning):
+    """(status, workspace bytes, staging bytes, block used)."""
+    ws = ctypes.c_size_t(0)
+    stg = ctypes.c_size_t(0)
+    blk = ctypes.c_int64(0)
+    st = int(load().sos_filter_host_sizes(n_channels, kmax, ctypes.c_void_p(lengths_host),
+                                          int(block), _tuning(tuning), ctypes.byref(ws),
+                                          ctypes.byref(stg), ctypes.byref(blk)))
+    return st, ws.value, stg.value, blk.value
+
+
+def sos_filter_host(x_host, sos, K, n_channels, kmax, lengths, lengths_host, zi, y_host, zf, ws,
+                    ws_bytes, staging, staging_bytes, block, tuning, stream) -> int:
+    """All pointer arguments are integers (0 for NULL); x_host, y_host host."""
+    V = ctypes.c_void_p
+    return int(load().sos_filter_host(V(x_host), V(sos), V(K), n_channels, kmax, V(lengths),
+                                      V(lengths_host), V(zi or None), V(y_host), V(zf or None),
+                                      V(ws), ws_bytes, V(staging), staging_bytes, int(block),
+                                      _tuning(tuning), V(stream)))
 
 
 def sos_prepare(sos, K, n_channels, kmax, lengths, lengths_host, ws, ws_bytes, tuning,

@@ -13,7 +13,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libsosfilt.so")
 SOURCES = ["plan.cu", "forward.cu", "pipe.cu", "warpseg.cu", "bwd.cu", "api.cu", "static_ws.cu",
-           "filtfilt.cu", "compare.cu"]
+           "filtfilt.cu", "compare.cu", "host_path.cu"]
 HEADERS = ["sos_common.cuh", "sos_df.cuh", "sos_kernels.cuh", "sos_async.cuh", "sos_pipe.cuh", "pipe_section.cuh"]
 INCLUDE = os.path.join(os.path.dirname(HERE), "include", "sosfilt.h")
 
