@@ -44,7 +44,7 @@
 
 namespace sosf {
 
-constexpr int kBwWarps = 2;  // warps per CTA
+constexpr int kBwWarps = 1;  // warps per CTA (one: shared memory, not threads, bounds the CTAs per SM)
 constexpr int kBwThreads = kBwWarps * 32;
 
 template <int N>
