@@ -8,7 +8,7 @@
 // the segment is a sequence of groups of N*L samples (L = 32 lanes), and each
 // section carries its DF2T state from one group to the next.
 //
-// One CTA runs a pipeline of warps over its segments:
+// One CTA per SM runs two pipelines of warps, each over its own segments:
 //   warp 0             loader: global -> a ring of shared-memory slots (one
 //                      group each, swizzled), by asynchronous copies;
 //   warp 1 + k         section k: for every group, in order, reads the group
@@ -104,7 +104,7 @@ __device__ __forceinline__ void pipe_segment_section(const Params& p, const SegG
 }
 
 template <int N, bool ZFK>
-__global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
+__global__ void __launch_bounds__(2 * kPipeThreads, 1) sos_pipe_kernel(Params p) {
     using PC = PipeCfg<N>;
     using SL = SlotLayout<N>;
     // the look-back kernel queued behind this one may be launched now (it
@@ -114,19 +114,29 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     // its writes) before the first read of the plan's tables
     asm volatile("griddepcontrol.wait;" ::: "memory");
     extern __shared__ float4 s_ring4[];
-    float* ring = reinterpret_cast<float*>(s_ring4);
-    __shared__ PipeShared sh;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __shared__ PipeShared sh2[2];
+    const int tid = threadIdx.x, lane = tid & 31, warp2 = tid >> 5;
+    // two pipelines per CTA, their warps interleaved (even warps pipeline 0,
+    // odd warps pipeline 1): the schedulers then favour neither, where two
+    // CTAs of one pipeline each on an SM finished 10-12 us apart
+    const int pl = warp2 & 1, warp = warp2 >> 1;
+    PipeShared& sh = sh2[pl];
+    float* ring = reinterpret_cast<float*>(s_ring4) + (size_t)pl * SL::kFloats * kPipeRing;
     const int64_t total = p.hdr->total_pipe;  // pipeline segments of the latest plan
 
-    for (int i = tid; i < kPipeRing; i += blockDim.x) {
+    for (int i = tid; i < 2 * kPipeRing; i += blockDim.x) {
         // every hand-over is an arrival of all 32 lanes of the handing warp
         // (for the loader: completion of each lane's copies)
-        for (int j = 0; j < kPipeStages; ++j) mbar_init(&sh.bar[i][j], 32);
-        mbar_init(&sh.free_[i], 32);
+        PipeShared& q = sh2[i / kPipeRing];
+        for (int j = 0; j < kPipeStages; ++j) mbar_init(&q.bar[i % kPipeRing][j], 32);
+        mbar_init(&q.free_[i % kPipeRing], 32);
     }
-    if (tid == 0) sh.limit = wait_limit(p.hdr, kHandOffLimit);
+    if (tid == 0) {
+        sh2[0].limit = wait_limit(p.hdr, kHandOffLimit);
+        sh2[1].limit = sh2[0].limit;
+    }
     __syncthreads();
+    const int64_t d0 = 2 * (int64_t)blockIdx.x + pl, dstep = 2 * (int64_t)gridDim.x;
 
     // ring position of the next group (all warps walk the same sequence):
     // slot s, and the parity of the slot's current use
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
     unsigned use = 0;
     if (warp == 0) {
         // ---- loader ----
-        for (int64_t d = blockIdx.x; d < total; d += gridDim.x) {
+        for (int64_t d = d0; d < total; d += dstep) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             const float* src = p.x + sg.off + sg.cstart;
             int rem = (int)(sg.len - sg.cstart < 0x40000000 ? sg.len - sg.cstart : 0x40000000);
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
         asm volatile("cp.async.wait_all;" ::: "memory");
     } else if (warp == kPipeWarps - 1) {
         // ---- storer ----
-        for (int64_t d = blockIdx.x; d < total; d += gridDim.x) {
+        for (int64_t d = d0; d < total; d += dstep) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             float* dst = p.y ? p.y + sg.off + sg.cstart : nullptr;
             // group-relative store window [a, b)
@@ -200,7 +210,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) sos_pipe_kernel(Params p) {
         const int k = warp - 1;
         int cur_c = -1;
         float4 ab = make_float4(0.f, 0.f, 0.f, 0.f), misc = ab, lp = ab;
-        for (int64_t d = blockIdx.x; d < total; d += gridDim.x) {
+        for (int64_t d = d0; d < total; d += dstep) {
             const SegGeom sg = seg_geom<PC::kGroup>(p, d);
             if (k < sg.K) {
                 if (sg.c != cur_c) {
@@ -255,7 +265,7 @@ cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream, bool
                                                                : SOSF_PIPE(64, true))
                        : (p.N == 16 ? SOSF_PIPE(16, false) : p.N == 32 ? SOSF_PIPE(32, false)
                                                                 : SOSF_PIPE(64, false));
-    const size_t smem = sizeof(float) * 32 * (size_t)(p.N + 4) * kPipeRing;
+    const size_t smem = 2 * sizeof(float) * 32 * (size_t)(p.N + 4) * kPipeRing;
     static bool attr[2][3] = {{false, false, false}, {false, false, false}};
     const int idx = p.N == 16 ? 0 : p.N == 32 ? 1 : 2;
     if (!attr[z][idx]) {
@@ -265,7 +275,7 @@ cudaError_t launch_pipe(const Params& p, int64_t grid, cudaStream_t stream, bool
         attr[z][idx] = true;
     }
     if (grid < 1) return cudaSuccess;
-    return launch_params(fn, grid, kPipeThreads, smem, p, stream, early);
+    return launch_params(fn, (grid + 1) / 2, 2 * kPipeThreads, smem, p, stream, early);
 }
 
 }  // namespace sosf
