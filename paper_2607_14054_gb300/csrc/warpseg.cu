@@ -22,10 +22,13 @@ namespace sosf {
 constexpr int kWsWarps = 4;  // warps per CTA
 constexpr int kWsThreads = kWsWarps * 32;
 
-// CTAs per SM the register budget is sized for (shared memory allows as many)
+// CTAs per SM the register budget is sized for (shared memory allows more):
+// three, 168 registers per thread.  At four (128 registers) the section
+// loop spilled (3.3 local loads per section and group on the band-pass) and
+// the kernel ran 16-22 % slower at N = 16 and 32 than at three with room.
 template <int N>
 constexpr int ws_ctas_per_sm() {
-    return N == 16 ? 4 : N == 32 ? 4 : 3;
+    return 3;
 }
 
 template <int N>
