@@ -57,8 +57,8 @@ def ws_ctas(n: int) -> int:
 # flags for the channels within their memory horizon: the warp-segment kernel
 # at the most CTAs per SM that fit and at fewer (longer-running warps, for
 # calls whose segments fill the GPU about once), and the section pipeline
-KERNELS = {16: (0, ws_ctas(3), SECTION_PIPELINE),
-           32: (0, ws_ctas(3), ws_ctas(2), SECTION_PIPELINE),
+KERNELS = {16: (0, ws_ctas(2), SECTION_PIPELINE),
+           32: (0, ws_ctas(2), SECTION_PIPELINE),
            64: (0, ws_ctas(2), SECTION_PIPELINE)}
 
 
