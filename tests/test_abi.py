@@ -68,3 +68,21 @@ def test_filter_rejects_bad_arguments_on_host(lib):
                            dummy, 16, None, 0) == -5               # workspace too small
     assert _abi.sos_filter(dummy, dummy, dummy, 1, 2, dummy, lengths.ctypes.data, 0, dummy + 8, 0,
                            dummy, 1 << 20, None, 0) == -1          # y overlaps x
+
+
+def test_host_path_sizes_on_host(lib):
+    """sos_filter_host_sizes answers on the host: the block is rounded up to
+    whole float4s, an eighth of the signal (at least 2^20) by default, the
+    staging area holds four block buffers, and negative lengths or too many
+    sections are refused."""
+    lh = np.array([3_000_000, 5, 0, 700_001], dtype=np.int64)
+    st, ws, stg, blk = _abi.sos_filter_host_sizes(4, 8, lh.ctypes.data, 1001, None)
+    assert st == 0 and blk == 1004 and ws > 0 and stg >= 4 * 4 * 1004
+    st, ws2, stg2, blk2 = _abi.sos_filter_host_sizes(4, 8, lh.ctypes.data, 0, None)
+    assert st == 0 and blk2 == 1 << 20 and stg2 >= 4 * 4 * (1 << 20)
+    big = np.array([1 << 26], dtype=np.int64)
+    st, _, _, blk3 = _abi.sos_filter_host_sizes(1, 2, big.ctypes.data, 0, None)
+    assert st == 0 and blk3 == (1 << 26) // 8
+    bad = np.array([10, -1], dtype=np.int64)
+    assert _abi.sos_filter_host_sizes(2, 2, bad.ctypes.data, 0, None)[0] == -1
+    assert _abi.sos_filter_host_sizes(1, 9, big.ctypes.data, 0, None)[0] == -1
