@@ -271,7 +271,9 @@ sos_status sos_stream(const float *x, float *y, const float *zi, float *zf, int3
  *   block           samples per block (<= 0: an eighth of the signal, at
  *                   least 2^20)
  * Asynchronous on `stream`: y_host holds the output once `stream` has
- * completed the call's work.  SOS_ERR_WORKSPACE if a buffer is too small;
+ * completed the call's work; after an error part way, `stream` still waits
+ * for the copies already enqueued, so that the buffers may be released once
+ * it is done.  SOS_ERR_WORKSPACE if a buffer is too small;
  * refused (SOS_ERR_ARG) while `stream` is being captured.  Calls on one
  * device enqueue in turn (a library mutex); their copies share the library's
  * two copy streams. */

@@ -31,7 +31,7 @@ constexpr int kMaxDevices = 64;
 struct HostPipe {
     cudaStream_t in = nullptr, out = nullptr;
     cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr},
-                ev_out[2] = {nullptr, nullptr}, ev_start = nullptr;
+                ev_out[2] = {nullptr, nullptr}, ev_start = nullptr, ev_join[2] = {nullptr, nullptr};
 };
 std::mutex g_host_mu;
 HostPipe g_pipes[kMaxDevices];
@@ -47,6 +47,8 @@ cudaError_t host_pipe(int dev, HostPipe** hp) {
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev_out[i], cudaEventDisableTiming);
         }
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h.ev_start, cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&h.ev_join[i], cudaEventDisableTiming);
         if (e != cudaSuccess) {
             h.in = nullptr;
             return e;
@@ -100,6 +102,61 @@ int64_t default_block(int64_t total) {
     int64_t b = (total + 7) / 8;
     b = (b + 4095) / 4096 * 4096;
     return std::max<int64_t>(b, int64_t(1) << 20);
+}
+
+// The blocks' copies in, filters and copies out, in order (see sos_filter_host).
+sos_status enqueue_blocks(const std::vector<Block>& blocks, HostPipe* hp, cudaStream_t st,
+                          const float* x_host, const double* sos, const int32_t* K, int32_t kmax,
+                          const int64_t* lengths, const int64_t* lengths_host, const float* zi,
+                          float* y_host, float* zf, void* workspace, size_t ws_bytes,
+                          float* const* dx, float* const* dy, float* const* carry,
+                          int64_t* const* lcell, const sos_tuning* tuning, void* stream) {
+    sos_status s = SOS_OK;
+    int pc = 0;  // carry buffer holding the state entering the next piece
+    for (size_t i = 0; i < blocks.size(); ++i) {
+        const Block& b = blocks[i];
+        const int sl = (int)(i & 1);
+        const size_t bytes = sizeof(float) * (size_t)b.len;
+        // copy in (after block i - 2's filter has released this buffer)
+        if (cudaStreamWaitEvent(hp->in, hp->ev_comp[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
+        if (b.len > 0 &&
+            cudaMemcpyAsync(dx[sl], x_host + b.off, bytes, cudaMemcpyHostToDevice, hp->in) !=
+                cudaSuccess)
+            return SOS_ERR_CUDA;
+        if (cudaEventRecord(hp->ev_in[sl], hp->in) != cudaSuccess) return SOS_ERR_CUDA;
+        // filter on the caller's stream (after the copy in, and after block
+        // i - 2's copy out has released the output buffer)
+        if (cudaStreamWaitEvent(st, hp->ev_in[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
+        if (cudaStreamWaitEvent(st, hp->ev_out[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
+        if (b.piece) {
+            const int32_t c = b.c0;
+            const int64_t len = b.len;
+            set_length_kernel<<<1, 1, 0, st>>>(lcell[sl], len);
+            if (cudaGetLastError() != cudaSuccess) return SOS_ERR_CUDA;
+            const float* zin = b.first ? (zi ? zi + (int64_t)c * kmax * 2 : nullptr) : carry[pc];
+            float* zout = b.last ? (zf ? zf + (int64_t)c * kmax * 2 : nullptr) : carry[pc ^ 1];
+            s = sos_filter(dx[sl], sos + (int64_t)c * kmax * 6, K + c, 1, kmax, lcell[sl], &len,
+                           zin, dy[sl], zout, workspace, ws_bytes, tuning, stream);
+            if (s != SOS_OK) return s;
+            if (!b.first || !b.last) pc ^= 1;
+        } else {
+            const int32_t c = b.c0, n = b.c1 - b.c0;
+            s = sos_filter(dx[sl], sos + (int64_t)c * kmax * 6, K + c, n, kmax, lengths + c,
+                           lengths_host + c, zi ? zi + (int64_t)c * kmax * 2 : nullptr, dy[sl],
+                           zf ? zf + (int64_t)c * kmax * 2 : nullptr, workspace, ws_bytes, tuning,
+                           stream);
+            if (s != SOS_OK) return s;
+        }
+        if (cudaEventRecord(hp->ev_comp[sl], st) != cudaSuccess) return SOS_ERR_CUDA;
+        // copy out
+        if (cudaStreamWaitEvent(hp->out, hp->ev_comp[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
+        if (b.len > 0 &&
+            cudaMemcpyAsync(y_host + b.off, dy[sl], bytes, cudaMemcpyDeviceToHost, hp->out) !=
+                cudaSuccess)
+            return SOS_ERR_CUDA;
+        if (cudaEventRecord(hp->ev_out[sl], hp->out) != cudaSuccess) return SOS_ERR_CUDA;
+    }
+    return SOS_OK;
 }
 
 }  // namespace
@@ -182,52 +239,17 @@ extern "C" sos_status sos_filter_host(const float* x_host, const double* sos, co
     if (cudaEventRecord(hp->ev_start, st) != cudaSuccess) return SOS_ERR_CUDA;
     if (cudaStreamWaitEvent(hp->in, hp->ev_start, 0) != cudaSuccess) return SOS_ERR_CUDA;
     if (cudaStreamWaitEvent(hp->out, hp->ev_start, 0) != cudaSuccess) return SOS_ERR_CUDA;
-    int pc = 0;  // carry buffer holding the state entering the next piece
-    for (size_t i = 0; i < blocks.size(); ++i) {
-        const Block& b = blocks[i];
-        const int sl = (int)(i & 1);
-        const size_t bytes = sizeof(float) * (size_t)b.len;
-        // copy in (after block i - 2's filter has released this buffer)
-        if (cudaStreamWaitEvent(hp->in, hp->ev_comp[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
-        if (b.len > 0 &&
-            cudaMemcpyAsync(dx[sl], x_host + b.off, bytes, cudaMemcpyHostToDevice, hp->in) !=
-                cudaSuccess)
-            return SOS_ERR_CUDA;
-        if (cudaEventRecord(hp->ev_in[sl], hp->in) != cudaSuccess) return SOS_ERR_CUDA;
-        // filter on the caller's stream (after the copy in, and after block
-        // i - 2's copy out has released the output buffer)
-        if (cudaStreamWaitEvent(st, hp->ev_in[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
-        if (cudaStreamWaitEvent(st, hp->ev_out[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
-        if (b.piece) {
-            const int32_t c = b.c0;
-            const int64_t len = b.len;
-            set_length_kernel<<<1, 1, 0, st>>>(lcell[sl], len);
-            if (cudaGetLastError() != cudaSuccess) return SOS_ERR_CUDA;
-            const float* zin = b.first ? (zi ? zi + (int64_t)c * kmax * 2 : nullptr) : carry[pc];
-            float* zout = b.last ? (zf ? zf + (int64_t)c * kmax * 2 : nullptr) : carry[pc ^ 1];
-            s = sos_filter(dx[sl], sos + (int64_t)c * kmax * 6, K + c, 1, kmax, lcell[sl], &len,
-                           zin, dy[sl], zout, workspace, ws_bytes, tuning, stream);
-            if (s != SOS_OK) return s;
-            if (!b.first || !b.last) pc ^= 1;
-        } else {
-            const int32_t c = b.c0, n = b.c1 - b.c0;
-            s = sos_filter(dx[sl], sos + (int64_t)c * kmax * 6, K + c, n, kmax, lengths + c,
-                           lengths_host + c, zi ? zi + (int64_t)c * kmax * 2 : nullptr, dy[sl],
-                           zf ? zf + (int64_t)c * kmax * 2 : nullptr, workspace, ws_bytes, tuning,
-                           stream);
-            if (s != SOS_OK) return s;
-        }
-        if (cudaEventRecord(hp->ev_comp[sl], st) != cudaSuccess) return SOS_ERR_CUDA;
-        // copy out
-        if (cudaStreamWaitEvent(hp->out, hp->ev_comp[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
-        if (b.len > 0 &&
-            cudaMemcpyAsync(y_host + b.off, dy[sl], bytes, cudaMemcpyDeviceToHost, hp->out) !=
-                cudaSuccess)
-            return SOS_ERR_CUDA;
-        if (cudaEventRecord(hp->ev_out[sl], hp->out) != cudaSuccess) return SOS_ERR_CUDA;
-    }
-    // the call is complete on `stream` when the last copies out are
-    for (int sl = 0; sl < 2; ++sl)
-        if (cudaStreamWaitEvent(st, hp->ev_out[sl], 0) != cudaSuccess) return SOS_ERR_CUDA;
-    return SOS_OK;
+    // the call is complete on `stream` when everything enqueued on the copy
+    // streams is: the last copies out, or, after an error part way, whatever
+    // was enqueued before it (so that the caller may free the buffers once
+    // `stream` is done)
+    const sos_status se = enqueue_blocks(blocks, hp, st, x_host, sos, K, kmax, lengths,
+                                         lengths_host, zi, y_host, zf, workspace, ws_bytes, dx,
+                                         dy, carry, lcell, tuning, stream);
+    cudaError_t e = cudaEventRecord(hp->ev_join[0], hp->in);
+    if (e == cudaSuccess) e = cudaEventRecord(hp->ev_join[1], hp->out);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp->ev_join[0], 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, hp->ev_join[1], 0);
+    if (se != SOS_OK) return se;
+    return e == cudaSuccess ? SOS_OK : SOS_ERR_CUDA;
 }
