@@ -327,7 +327,8 @@ __device__ bool horizon_poles(const double (*rows)[5], const float (*rowsf)[5], 
 struct HandoffScratch {
     cpx W[2 * kMaxSections][2 * kMaxSections];  // q_ij / (1 - q_ij)
     cpx F[2 * kMaxSections][kMaxSections];      // F_i(m)
-    cpx R[2 * kMaxSections];                    // residues of the current cascade
+    cpx R[2 * kMaxSections][2 * kMaxSections];  // residues: [cascade t][pole i]
+    float h0[2 * kMaxSections];                 // direct term of cascade t
     float E[2 * kMaxSections];                  // prefix (0..K-1) and suffix energies
 };
 
@@ -388,35 +389,58 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
     }
     __syncwarp();
     // the energies: cascade t < K is the prefix 0..t, t >= K the suffix
-    // (t - K + 1)..K-1; lane i's residue is the product of its F_i over the
-    // cascade's sections, the pair sum is spread over the whole warp
-    bool ok = true;
-#pragma unroll 1
-    for (int t = 0; t < 2 * K - 1; ++t) {
+    // (t - K + 1)..K-1.  First, for every cascade at once (lane t), its
+    // direct term h0 (the product of its sections' b0 over their scales,
+    // left to right); and (lane i) pole i's residue in every cascade that
+    // holds its section, the product of its F_i over the cascade's sections
+    // (left to right: prefixes grow by one factor, suffixes are formed
+    // whole), zero in the others
+    if (lane < 2 * K - 1) {
+        const int t = lane;
         const bool pre = t < K;
         const int a = pre ? 0 : t - K + 1, b = pre ? t : K - 1;
         float h0 = 1.f;
 #pragma unroll 1
         for (int m = a; m <= b; ++m) h0 *= rowsf[m][0] / num_scale(rowsf[m]);
-        if (lane < np) {
-            const int sec = lane >> 1;
-            cpx R{0.f, 0.f};
-            if (sec >= a && sec <= b) {
-                R = cpx{1.f, 0.f};
-#pragma unroll 1
-                for (int m = a; m <= b; ++m) R = cmul(R, hs.F[lane][m]);
+        hs.h0[t] = h0;
+    }
+    if (lane < np) {
+        const int sec = lane >> 1;
+        cpx f[kMaxSections];
+#pragma unroll
+        for (int m = 0; m < kMaxSections; ++m) f[m] = m < K ? hs.F[lane][m] : cpx{1.f, 0.f};
+        cpx P{1.f, 0.f};
+#pragma unroll
+        for (int t = 0; t < kMaxSections; ++t) {
+            if (t < K) {
+                P = cmul(P, f[t]);
+                hs.R[t][lane] = sec <= t ? P : cpx{0.f, 0.f};
             }
-            hs.R[lane] = R;
         }
-        __syncwarp();
+#pragma unroll
+        for (int a = 1; a < kMaxSections; ++a) {
+            if (a < K) {
+                cpx S{1.f, 0.f};
+#pragma unroll
+                for (int m = 0; m < kMaxSections; ++m)
+                    if (m >= a && m < K) S = cmul(S, f[m]);
+                hs.R[K - 1 + a][lane] = sec >= a ? S : cpx{0.f, 0.f};
+            }
+        }
+    }
+    __syncwarp();
+    bool ok = true;
+#pragma unroll 1
+    for (int t = 0; t < 2 * K - 1; ++t) {
+        const float h0 = hs.h0[t];
         // pair (i, j): lane handles i = lane & 15 and half of the j
         float e = 0.f, ea = 0.f;
         const int i = lane & 15;
         if (i < np) {
-            const cpx Ri = hs.R[i];
-#pragma unroll 1
+            const cpx Ri = hs.R[t][i];
+#pragma unroll 2
             for (int j = lane >> 4; j < np; j += 2) {
-                const cpx Rj = hs.R[j];
+                const cpx Rj = hs.R[t][j];
                 const cpx tt = cmul(cmul(Ri, cpx{Rj.re, -Rj.im}), hs.W[i][j]);
                 e += tt.re;
                 ea += sqrtf(fmaf(tt.re, tt.re, tt.im * tt.im));
