@@ -473,6 +473,58 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
     return 0x1p-24f * fmaxf(amp, 1.f);
 }
 
+// A memory horizon without partial fractions, for cascades whose poles
+// coincide (or nearly so) and so have none to use: with r the largest pole
+// modulus, each section's all-pole response is bounded by (n + 1) r^n and its
+// whole response by B_k r^-2 (n + 1) r^n (B_k = |b0| + |b1| + |b2|), so the
+// cascade's by A C(n + 2K - 1, 2K - 1) r^n with A = prod_k B_k r^-2 (the
+// coefficients of 1 / (1 - r z)^(2K)).  Past the terms' peak the tail sum
+// from P on is at most the term at P over (1 - its ratio to the next); P is
+// the first point where that is below kHorizonEps h2 (found by bisection on
+// the log of the bound).  Far more conservative than the partial-fraction
+// horizon, but it holds for repeated poles.  -1 where r >= 1 or no such P
+// below 2^30.  One thread.
+__device__ int horizon_fallback(const double (*rows)[5], int K, float h2) {
+    if (K < 1 || !(h2 > 0.f)) return -1;
+    double r = 0.0, logA = 0.0;
+    for (int k = 0; k < K; ++k) {
+        const double a1 = rows[k][3], a2 = rows[k][4];
+        const double disc = a1 * a1 - 4.0 * a2;
+        double rk;
+        if (disc < 0.0) {
+            rk = sqrt(a2);
+        } else {
+            const double sq = sqrt(disc);
+            rk = fmax(fabs(0.5 * (-a1 + sq)), fabs(0.5 * (-a1 - sq)));
+        }
+        r = fmax(r, rk);
+        const double B = fabs(rows[k][0]) + fabs(rows[k][1]) + fabs(rows[k][2]);
+        if (!(B > 0.0) || !isfinite(B)) return -1;
+        logA += log(B);
+    }
+    if (!(r < 1.0 - 1e-12)) return -1;
+    if (r < 1e-300) return ((2 * K + 1) + 15) / 16 * 16;  // a finite response
+    logA -= 2.0 * K * log(r);
+    const double m = 2.0 * K, lr = log(r);
+    const double target = log((double)kHorizonEps * (double)h2);
+    // log of the tail bound from n on, for n past the peak (ratio < 1)
+    auto tail = [&](double n) {
+        const double ratio = r * (n + m) / (n + 1.0);
+        return logA + lgamma(n + m) - lgamma(m) - lgamma(n + 1.0) + n * lr - log1p(-ratio);
+    };
+    double lo = fmax(ceil((m * r - 1.0) / (1.0 - r)) + 1.0, m);
+    double hi = 1073741824.0;
+    if (!(tail(hi) <= target)) return -1;
+    if (tail(lo) <= target) hi = lo;
+    for (int it = 0; it < 40 && hi - lo > 1.0; ++it) {
+        const double mid = floor(0.5 * (lo + hi));
+        if (tail(mid) <= target) hi = mid;
+        else lo = mid;
+    }
+    const int64_t P = ((int64_t)hi + 15) / 16 * 16;
+    return P < (int64_t)1 << 30 ? (int)P : -1;
+}
+
 // The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp), and
 // the channel's segment length: the call's T, or longer when the horizon
 // needs it (a segment is at least 2 P and long enough for the initial
@@ -758,8 +810,24 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         int P = carry_only ? -1
                            : horizon_combine(ok, h2, Kc, p.seg, 32LL * p.N, la, ilr, zs, lr, seg,
                                              minseg, minseg_z);
-        // backward plans have no look-back: a channel without a horizon is
-        // one segment, run from its start to its end by one pipeline
+        // backward plans have no look-back: a channel without a partial-
+        // fraction horizon (repeated poles) takes the cruder bound, so that it
+        // is still cut into segments (warm-ups of P on both sides)
+        if (P < 0 && !carry_only && Kc > 0 && (p.flags_opt & kFlagBackwardPlan)) {
+            int Pf = 0;
+            if (lane == 0) Pf = horizon_fallback(s_row, Kc, s_h2);
+            Pf = __shfl_sync(0xffffffffu, Pf, 0);
+            if (Pf >= 0) {
+                const int64_t G = 32LL * p.N, want = 2LL * Pf;
+                P = Pf;
+                seg = p.seg;
+                if (want > seg) seg = (want + G - 1) / G * G;
+                minseg = (int32_t)((Pf + G - 1) / G * G > G ? (Pf + G - 1) / G * G : G);
+                minseg_z = minseg;
+            }
+        }
+        // and a channel with no horizon at all is one segment, run from its
+        // start to its end by one pipeline
         const int single = (P < 0 && (p.flags_opt & kFlagBackwardPlan)) ? 1 : 0;
         if (single) P = 0;
         if (lane == 0) {

@@ -206,3 +206,41 @@ def test_adjoint_long_memory_several_segments():
     assert st == 0
     assert (h > 1000).all() and (t >= 4).all(), (h, t)
     print("long-memory adjoint", worst, "horizons", h.tolist(), "segments", t.tolist())
+
+
+def test_adjoint_repeated_poles_several_segments():
+    """Cascades whose sections come in identical pairs (repeated poles, as
+    in Linkwitz-Riley filters) have no partial-fraction memory horizon; the
+    backward plan bounds their memory without one (C(n + 2K - 1, 2K - 1) r^n
+    over the largest pole radius r) and still cuts long channels into
+    segments: every gradient group within 1e-4 of the oracle adjoint."""
+    from synth import filters
+    P = _lib()
+    C, kmax, n = 4, 4, 1 << 19
+    lengths = torch.full((C,), n, dtype=torch.int64)
+    K = torch.full((C,), kmax, dtype=torch.int32)
+    sos = np.zeros((C, kmax, 6))
+    for c in range(C):
+        half = filters.random_sections(800 + c, kmax // 2, 0.95, 0.99)
+        sos[c, 0::2] = half
+        sos[c, 1::2] = half
+    sos = torch.from_numpy(sos)
+    x = rng.normal(801, rng.STREAM_SIGNAL, C * n)
+    zi = rng.normal(801, rng.STREAM_STATE, C * kmax * 2).view(C, kmax, 2)
+    gy = rng.normal(802, rng.STREAM_SIGNAL, C * n)
+    gzf = rng.normal(803, rng.STREAM_STATE, C * kmax * 2).view(C, kmax, 2)
+    got, ref = run_both(x, sos, K, lengths, zi, gy, gzf)
+    worst = check_grads(got, ref, lengths.numpy(), K.numpy(), 1e-4)
+    plan = P.SosFilter(lengths, kmax)
+    plan.backward(x.cuda(), sos.cuda(), K.cuda(), zi.cuda(), gy.cuda(), gzf.cuda())
+    h = torch.empty(C, dtype=torch.int32)
+    t = torch.empty(C, dtype=torch.int32)
+    st = P._abi.sos_plan_query(plan._bws.data_ptr(), 0, C, h.data_ptr(), t.data_ptr(),
+                               torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    assert (h > 0).all() and (t >= 4).all(), (h, t)
+    # the forward plan of the same cascades keeps the look-back (no horizon)
+    plan.prepare(sos.cuda(), K.cuda())
+    hf, _ = plan.plan_info()
+    assert (hf < 0).all(), hf
+    print("repeated-pole adjoint", worst, "horizons", h.tolist(), "segments", t.tolist())
