@@ -386,7 +386,11 @@ size_t sos_backward_workspace_size(int32_t n_channels, int32_t kmax, const int64
  * the section states at group starts (checkpoints, in the workspace), and the
  * adjoint pass recomputes each group's section inputs from its checkpoint in
  * shared memory just before running that group backwards.
- * Channels without a memory horizon run as one segment each (correct, but
+ * Channels are cut into segments warmed up over their memory horizon on both
+ * sides; cascades whose poles coincide get a cruder horizon that needs no
+ * partial fractions (the largest pole radius r: a tail bound of the form
+ * C(n + 2K - 1, 2K - 1) r^n).  Channels with no horizon at all (a pole
+ * within 1e-12 of the unit circle) run as one segment each (correct, but
  * without parallelism inside the channel).  Asynchronous on `stream`;
  * argument errors are returned at once, device errors go to the status word. */
 sos_status sos_filter_backward(const float *x, const double *sos, const int32_t *K,
