@@ -482,11 +482,14 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
 // from P on is at most the term at P over (1 - its ratio to the next); P is
 // the first point where that is below kHorizonEps h2 (found by bisection on
 // the log of the bound).  Far more conservative than the partial-fraction
-// horizon, but it holds for repeated poles.  -1 where r >= 1 or no such P
-// below 2^30.  One thread.
-__device__ int horizon_fallback(const double (*rows)[5], int K, float h2) {
+// horizon, but it holds for repeated poles.  tz: the same for the response
+// of a unit initial state (it enters a section's recursion like an impulse
+// of at most unit size, so B_k is taken as at least 1).  -1 where r >= 1 or
+// no such P below 2^30.  One thread.
+__device__ int horizon_fallback(const double (*rows)[5], int K, float h2, int& tz) {
+    tz = -1;
     if (K < 1 || !(h2 > 0.f)) return -1;
-    double r = 0.0, logA = 0.0;
+    double r = 0.0, logA = 0.0, logAs = 0.0;
     for (int k = 0; k < K; ++k) {
         const double a1 = rows[k][3], a2 = rows[k][4];
         const double disc = a1 * a1 - 4.0 * a2;
@@ -501,28 +504,38 @@ __device__ int horizon_fallback(const double (*rows)[5], int K, float h2) {
         const double B = fabs(rows[k][0]) + fabs(rows[k][1]) + fabs(rows[k][2]);
         if (!(B > 0.0) || !isfinite(B)) return -1;
         logA += log(B);
+        logAs += log(fmax(B, 1.0));
     }
     if (!(r < 1.0 - 1e-12)) return -1;
-    if (r < 1e-300) return ((2 * K + 1) + 15) / 16 * 16;  // a finite response
-    logA -= 2.0 * K * log(r);
+    if (r < 1e-300) {  // a finite response
+        tz = ((2 * K + 1) + 15) / 16 * 16;
+        return tz;
+    }
     const double m = 2.0 * K, lr = log(r);
     const double target = log((double)kHorizonEps * (double)h2);
-    // log of the tail bound from n on, for n past the peak (ratio < 1)
-    auto tail = [&](double n) {
-        const double ratio = r * (n + m) / (n + 1.0);
-        return logA + lgamma(n + m) - lgamma(m) - lgamma(n + 1.0) + n * lr - log1p(-ratio);
+    // the first n past the peak (ratio < 1) where the log tail bound with
+    // prefactor log a is below the target, in multiples of 16; -1 if none
+    auto first = [&](double loga) -> int {
+        auto tail = [&](double n) {
+            const double ratio = r * (n + m) / (n + 1.0);
+            return loga + lgamma(n + m) - lgamma(m) - lgamma(n + 1.0) + n * lr - log1p(-ratio);
+        };
+        double lo = fmax(ceil((m * r - 1.0) / (1.0 - r)) + 1.0, m);
+        double hi = 1073741824.0;
+        if (!(tail(hi) <= target)) return -1;
+        if (tail(lo) <= target) hi = lo;
+        for (int it = 0; it < 40 && hi - lo > 1.0; ++it) {
+            const double mid = floor(0.5 * (lo + hi));
+            if (tail(mid) <= target) hi = mid;
+            else lo = mid;
+        }
+        const int64_t n = ((int64_t)hi + 15) / 16 * 16;
+        return n < (int64_t)1 << 30 ? (int)n : -1;
     };
-    double lo = fmax(ceil((m * r - 1.0) / (1.0 - r)) + 1.0, m);
-    double hi = 1073741824.0;
-    if (!(tail(hi) <= target)) return -1;
-    if (tail(lo) <= target) hi = lo;
-    for (int it = 0; it < 40 && hi - lo > 1.0; ++it) {
-        const double mid = floor(0.5 * (lo + hi));
-        if (tail(mid) <= target) hi = mid;
-        else lo = mid;
-    }
-    const int64_t P = ((int64_t)hi + 15) / 16 * 16;
-    return P < (int64_t)1 << 30 ? (int)P : -1;
+    const int P = first(logA - 2.0 * K * lr);
+    if (P < 0) return -1;
+    tz = first(logAs - 2.0 * K * lr);
+    return tz < 0 ? -1 : P;
 }
 
 // The horizon from the per-pole terms and ||h||_2 >= h2 (the pole warp), and
@@ -810,20 +823,26 @@ __device__ __forceinline__ bool plan_channel(const Params& p) {
         int P = carry_only ? -1
                            : horizon_combine(ok, h2, Kc, p.seg, 32LL * p.N, la, ilr, zs, lr, seg,
                                              minseg, minseg_z);
-        // backward plans have no look-back: a channel without a partial-
-        // fraction horizon (repeated poles) takes the cruder bound, so that it
-        // is still cut into segments (warm-ups of P on both sides)
-        if (P < 0 && !carry_only && Kc > 0 && (p.flags_opt & kFlagBackwardPlan)) {
-            int Pf = 0;
-            if (lane == 0) Pf = horizon_fallback(s_row, Kc, s_h2);
+        // a channel without a partial-fraction horizon (repeated poles)
+        // takes the cruder bound: always in backward plans, which have no
+        // look-back (so that it is still cut into segments, warm-ups of P on
+        // both sides), and in forward plans where the channel is long enough
+        // for at least eight segments (the look-back is faster below that)
+        if (P < 0 && !carry_only && Kc > 0) {
+            int Pf = -1, tzf = -1;
+            if (lane == 0) Pf = horizon_fallback(s_row, Kc, s_h2, tzf);
             Pf = __shfl_sync(0xffffffffu, Pf, 0);
-            if (Pf >= 0) {
-                const int64_t G = 32LL * p.N, want = 2LL * Pf;
+            tzf = __shfl_sync(0xffffffffu, tzf, 0);
+            const int64_t want = Pf >= 0 ? (2LL * Pf > tzf ? 2LL * Pf : (int64_t)tzf) : 0;
+            const int64_t lenc = p.lengths[c];
+            if (Pf >= 0 && ((p.flags_opt & kFlagBackwardPlan) || lenc >= 8 * want)) {
+                const int64_t G = 32LL * p.N;
                 P = Pf;
                 seg = p.seg;
                 if (want > seg) seg = (want + G - 1) / G * G;
                 minseg = (int32_t)((Pf + G - 1) / G * G > G ? (Pf + G - 1) / G * G : G);
-                minseg_z = minseg;
+                minseg_z = (int32_t)((tzf + G - 1) / G * G > minseg ? (tzf + G - 1) / G * G
+                                                                     : minseg);
             }
         }
         // and a channel with no horizon at all is one segment, run from its

@@ -166,22 +166,26 @@ def test_precision_stress_short_channels_all_tunings():
 @pytest.mark.parametrize("wn", [0.002, 0.005])
 def test_low_cutoff_linkwitz_riley_on_the_look_back(wn):
     """Two identical 2nd-order Butterworth low-pass sections (a 4th-order
-    Linkwitz-Riley crossover) at a low cutoff: coincident poles, so no memory
-    horizon (the look-back carries the state, in FP32 scans), and poles close
+    Linkwitz-Riley crossover) at a low cutoff: coincident poles, so no
+    partial-fraction memory horizon; with the look-back forced
+    (SOS_FLAG_CARRY_ONLY) the state is carried in FP32 scans, and poles close
     to z = 1 (ill-conditioned: flagged).  The look-back's composition keeps
-    the error well inside 1e-3 here."""
+    the error well inside 1e-3 here; the default plan (the partial-fraction-
+    free horizon where the channel is long enough) as well."""
     from synth import filters, rng
     P = _lib()
     s1 = filters.butter_lowpass2_closed_form(wn)
     sos = np.concatenate([s1, s1])
     n = 1 << 20
     x = rng.normal(7, rng.STREAM_SIGNAL, n, device="cuda").float()
-    plan = P.SosFilter([n], 2)
-    y, _ = plan(x, torch.from_numpy(sos)[None].cuda(), torch.tensor([2], dtype=torch.int32).cuda(),
-                None)
-    assert plan.device_status() == 0
-    hz, _ = plan.plan_info()
-    assert int(hz[0]) == -1 and int(plan.plan_extended()[0]) >= 1
     ref, _ = oracle.sosfilt(x.double().cpu().numpy(), sos)
-    err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
-    assert err <= 1e-3, err
+    for tuning in [(0, 0, 0, 2), None]:
+        plan = P.SosFilter([n], 2, tuning=tuning)
+        y, _ = plan(x, torch.from_numpy(sos)[None].cuda(),
+                    torch.tensor([2], dtype=torch.int32).cuda(), None)
+        assert plan.device_status() == 0
+        hz, _ = plan.plan_info()
+        if tuning is not None:
+            assert int(hz[0]) == -1 and int(plan.plan_extended()[0]) >= 1
+        err = np.linalg.norm(y.double().cpu().numpy() - ref) / np.linalg.norm(ref)
+        assert err <= 1e-3, (tuning, int(hz[0]), err)
