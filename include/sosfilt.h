@@ -114,11 +114,14 @@ typedef enum sos_status {
  * 2^-30 relative.  The channel is then cut into segments of S samples (the
  * call's segment length, a multiple of 32 N chosen from its total length, or
  * 2 P rounded up to whole groups when that is longer) that each start P
- * samples early from zero state (no cross-segment dependency).  Where no
- * horizon can be bounded (a pole within 1e-7 of the unit circle, coincident
- * poles), the DF2T state of every section is carried by a decoupled
- * look-back composing FP64-accurate affine maps (Sec. V's group hand-off made
- * parallel). */
+ * samples early from zero state (no cross-segment dependency).  Coincident
+ * poles, where partial fractions fail, get a cruder bound over the largest
+ * pole radius r (a tail of the form C(n + 2K - 1, 2K - 1) r^n) when the
+ * channel is at least eight of the segments it asks for.  Where no horizon is
+ * bounded (a pole within 1e-7 of the unit circle, or coincident poles on a
+ * shorter channel), the DF2T state of every section is carried by a
+ * decoupled look-back composing FP64-accurate affine maps (Sec. V's group
+ * hand-off made parallel). */
 typedef struct sos_tuning {
     int32_t n_blocks;
     int32_t warps;
