@@ -133,17 +133,20 @@ __device__ __forceinline__ df df_dot3(df a0, df x0, df a1, df x1, df a2, df x2) 
     return df_fast_two_sum(s2.hi, c);
 }
 
-// u - a1*y1 - a2*y2: one step of the all-pole recursion
+// u - a1*y1 - a2*y2: one step of the all-pole recursion.  In a run, y1 is
+// the previous step's result, so it enters last: the older term a2*y2 and
+// every low-order term of a1*y1 are summed first, and only the TwoSum with
+// a1*y1's rounded product and the final renormalisation follow y1.hi.
 __device__ __forceinline__ df df_rec(df u, df a1, df y1, df a2, df y2) {
-    const float p1 = a1.hi * y1.hi, p2 = a2.hi * y2.hi;
-    float c = u.lo - fmaf(a1.hi, y1.hi, -p1);
-    c -= fmaf(a2.hi, y2.hi, -p2);
-    const df s1 = df_two_sum(u.hi, -p1);
-    const df s2 = df_two_sum(s1.hi, -p2);
-    c += s1.lo + s2.lo;
-    c = fmaf(-a1.hi, y1.lo, fmaf(-a1.lo, y1.hi, c));
+    const float p2 = a2.hi * y2.hi;
+    const df s1 = df_two_sum(u.hi, -p2);
+    float c = u.lo - fmaf(a2.hi, y2.hi, -p2);
     c = fmaf(-a2.hi, y2.lo, fmaf(-a2.lo, y2.hi, c));
-    return df_fast_two_sum(s2.hi, c);
+    c += s1.lo;
+    const float p1 = a1.hi * y1.hi;
+    const float c1 = fmaf(-a1.hi, y1.lo, fmaf(-a1.lo, y1.hi, -fmaf(a1.hi, y1.hi, -p1)));
+    const df s2 = df_two_sum(s1.hi, -p1);
+    return df_fast_two_sum(s2.hi, (c + c1) + s2.lo);
 }
 
 // u - a1*y1 (the second sample of a run, one history term)
