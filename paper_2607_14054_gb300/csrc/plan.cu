@@ -430,29 +430,41 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
     }
     __syncwarp();
     bool ok = true;
+    // two cascades per pass (ta, tb), their sums side by side: independent
+    // chains of loads, products and shuffles for the scheduler to overlap
 #pragma unroll 1
-    for (int t = 0; t < 2 * K - 1; ++t) {
-        const float h0 = hs.h0[t];
+    for (int ta = 0; ta < 2 * K - 1; ta += 2) {
+        const int tb = ta + 1 < 2 * K - 1 ? ta + 1 : ta;
         // pair (i, j): lane handles i = lane & 15 and half of the j
-        float e = 0.f, ea = 0.f;
+        float e = 0.f, ea = 0.f, f = 0.f, fa = 0.f;
         const int i = lane & 15;
         if (i < np) {
-            const cpx Ri = hs.R[t][i];
+            const cpx Ria = hs.R[ta][i], Rib = hs.R[tb][i];
 #pragma unroll 2
             for (int j = lane >> 4; j < np; j += 2) {
-                const cpx Rj = hs.R[t][j];
-                const cpx tt = cmul(cmul(Ri, cpx{Rj.re, -Rj.im}), hs.W[i][j]);
-                e += tt.re;
-                ea += sqrtf(fmaf(tt.re, tt.re, tt.im * tt.im));
+                const cpx Rja = hs.R[ta][j], Rjb = hs.R[tb][j], Wij = hs.W[i][j];
+                const cpx u = cmul(cmul(Ria, cpx{Rja.re, -Rja.im}), Wij);
+                const cpx v = cmul(cmul(Rib, cpx{Rjb.re, -Rjb.im}), Wij);
+                e += u.re;
+                ea += sqrtf(fmaf(u.re, u.re, u.im * u.im));
+                f += v.re;
+                fa += sqrtf(fmaf(v.re, v.re, v.im * v.im));
             }
         }
         for (int o = 16; o > 0; o >>= 1) {
             e += __shfl_xor_sync(0xffffffffu, e, o);
             ea += __shfl_xor_sync(0xffffffffu, ea, o);
+            f += __shfl_xor_sync(0xffffffffu, f, o);
+            fa += __shfl_xor_sync(0xffffffffu, fa, o);
         }
-        const float E = fmaf(h0, h0, e);
-        ok = ok && E > 0.f && E >= 1e-5f * ea && E < 1e30f;
-        if (lane == 0) hs.E[t] = E;
+        const float ha = hs.h0[ta], hb = hs.h0[tb];
+        const float Ea = fmaf(ha, ha, e), Eb = fmaf(hb, hb, f);
+        ok = ok && Ea > 0.f && Ea >= 1e-5f * ea && Ea < 1e30f;
+        ok = ok && Eb > 0.f && Eb >= 1e-5f * fa && Eb < 1e30f;
+        if (lane == 0) {
+            hs.E[ta] = Ea;
+            hs.E[tb] = Eb;
+        }
         __syncwarp();
     }
     if (__any_sync(0xffffffffu, bad) || !ok) return -1.f;
