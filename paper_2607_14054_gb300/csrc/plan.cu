@@ -353,38 +353,41 @@ __device__ float handoff_error(const double (*rows)[5], const float (*rowsf)[5],
     }
     __syncwarp();
     bool bad = false;
-    // lane i < 2K: W[i][j] and F[i][m]
-    if (lane < np) {
-        const cpx pi = s_pole[lane];
+    // W[i][j] and F[i][m] for pole i = lane & 15, the j and m split between
+    // the two half-warps (every entry on its own: the same values as one lane
+    // per pole, in half the steps)
+    const int ip = lane & 15, half = lane >> 4;
+    if (ip < np) {
+        const cpx pi = s_pole[ip];
         const float r2 = fmaf(pi.re, pi.re, pi.im * pi.im);
         if (!(r2 > 1e-24f)) bad = true;
         const float ir2 = r2 > 1e-24f ? 1.f / r2 : 0.f;
         const cpx inv{pi.re * ir2, -pi.im * ir2};
         const cpx inv2 = cmul(inv, inv);
 #pragma unroll 1
-        for (int j = 0; j < np; ++j) {
+        for (int j = half; j < np; j += 2) {
             const cpx pj = s_pole[j];
             const cpx q = cmul(pi, cpx{pj.re, -pj.im});
             const cpx d{1.f - q.re, -q.im};
             if (!(fmaf(d.re, d.re, d.im * d.im) > 1e-30f)) bad = true;
-            hs.W[lane][j] = cdiv(q, d);
+            hs.W[ip][j] = cdiv(q, d);
         }
 #pragma unroll 1
-        for (int m = 0; m < K; ++m) {
+        for (int m = half; m < K; m += 2) {
             const float ims = 1.f / num_scale(rowsf[m]);
             const float b0 = rowsf[m][0] * ims, b1 = rowsf[m][1] * ims, b2 = rowsf[m][2] * ims;
             cpx f{fmaf(b2, inv2.re, fmaf(b1, inv.re, b0)), fmaf(b2, inv2.im, b1 * inv.im)};
 #pragma unroll 1
             for (int u = 0; u < 2; ++u) {
                 const int l = 2 * m + u;
-                if (l != lane) {
+                if (l != ip) {
                     const cpx g = cmul(s_pole[l], inv);
                     const cpx h{1.f - g.re, -g.im};
                     if (fmaf(h.re, h.re, h.im * h.im) < 1e-8f) bad = true;
                     f = cdiv(f, h);
                 }
             }
-            hs.F[lane][m] = f;
+            hs.F[ip][m] = f;
         }
     }
     __syncwarp();
