@@ -115,3 +115,35 @@ def test_stream_long_blocks_cut_into_segments():
     for c in range(C):
         zf[c, int(K[c]):] = 0.0
     check(y.reshape(-1).cpu().numpy(), zf, y_ref, zf_ref, L.numpy(), K.numpy(), 1e-5)
+
+
+def test_stream_double_float_channels():
+    """Cascades the plan puts in precision class 3 (a double-float range of
+    sections around the hand-offs its error estimate blames), taken from the
+    batched workload's random bank, streamed in 4096-sample blocks: every
+    block through the class-3 segment code, against the one-shot oracle at
+    1e-5, final states included."""
+    P = _lib()
+    C, kmax = 4096, 8
+    K = rng.randint(3, rng.STREAM_SECTIONS, C, 1, kmax).to(torch.int32)
+    bank = workloads._random_bank(3, C, kmax, 0.5, 0.995, K.numpy())
+    probe = P.SosFilter([8192] * C, kmax)
+    probe.prepare(torch.from_numpy(bank).cuda(), K.cuda())
+    ext = probe.plan_extended().numpy()
+    pick = [int(c) for c in np.nonzero(ext == 3)[0][:4]]
+    assert len(pick) == 4, ext
+    sos = torch.from_numpy(bank[pick]).contiguous()
+    Kp = K[pick].contiguous()
+    T, chunk = 1 << 18, 4096
+    x = rng.normal(97, rng.STREAM_SIGNAL, 4 * T)
+    zi = rng.normal(98, rng.STREAM_STATE, 4 * kmax * 2).view(4, kmax, 2)
+    for c in range(4):
+        zi[c, int(Kp[c]):] = 0.0
+    y, state = _stream(P, x.view(4, T).cuda(), sos, Kp, zi, chunk, (16, 8, 1, 0))
+    L = torch.full((4,), T, dtype=torch.int64)
+    y_ref, zf_ref = oracle.sosfilt(x.double().numpy(), sos.numpy(), K=Kp.numpy(),
+                                   lengths=L.numpy(), zi=zi.double().numpy())
+    zf = state.cpu().numpy().copy()
+    for c in range(4):
+        zf[c, int(Kp[c]):] = 0.0
+    check(y.reshape(-1).cpu().numpy(), zf, y_ref, zf_ref, L.numpy(), Kp.numpy(), 1e-5)
