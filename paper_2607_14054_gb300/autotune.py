@@ -110,6 +110,8 @@ def _save_file(path: str) -> None:
 
 
 def _time_apply(plan, x, y, zi, zf, sos, K, reps: int) -> float:
+    """Best of `reps` timed calls as a caller makes them: prepare (its plan
+    cache holding the tables after the first) and apply."""
     plan.prepare(sos, K)
     plan.apply(x, y, zi, zf)  # warm-up (also first-launch attribute setup)
     torch.cuda.synchronize()
@@ -118,6 +120,7 @@ def _time_apply(plan, x, y, zi, zf, sos, K, reps: int) -> float:
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record()
+        plan.prepare(sos, K)
         plan.apply(x, y, zi, zf)
         e1.record()
         torch.cuda.synchronize()
@@ -126,7 +129,7 @@ def _time_apply(plan, x, y, zi, zf, sos, K, reps: int) -> float:
 
 
 def autotune(x: torch.Tensor, sos: torch.Tensor, K: Optional[torch.Tensor] = None,
-             lengths=None, zi: Optional[torch.Tensor] = None, reps: int = 3,
+             lengths=None, zi: Optional[torch.Tensor] = None, reps: int = 5,
              use_cache: bool = True, report: Optional[list] = None) -> Tuple[int, int, int, int]:
     """Fastest (N, W, algo, flags) for this call's shapes, by measurement."""
     from . import SosFilter
